@@ -1,0 +1,55 @@
+"""The seeded input generators: determinism and the structural properties
+each workload recipe promises (distinct edges, no self-loops, absent/present
+edges for insert/delete batches, append-only vertex ids)."""
+import numpy as np
+
+import synth
+
+
+def _keys(e):
+    e = np.asarray(e, dtype=np.int64)
+    lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
+    return lo << 32 | hi
+
+
+def test_er_distinct_and_deterministic():
+    a = synth.er(1000, 5000, synth.stream(1))
+    b = synth.er(1000, 5000, synth.stream(1))
+    assert (a == b).all() and len(np.unique(_keys(a))) == 5000
+    assert (a[:, 0] != a[:, 1]).all() and a.min() >= 0 and a.max() < 1000
+
+
+def test_rmat_canonical_unique():
+    e = synth.rmat(12, 8, synth.stream(2))
+    assert (e[:, 0] < e[:, 1]).all()
+    k = _keys(e)
+    assert (np.diff(k) > 0).all() and e.max() < 4096
+    # skewed degrees: the top vertex is far above the mean
+    deg = np.bincount(e.ravel(), minlength=4096)
+    assert deg.max() > 10 * deg.mean()
+
+
+def test_ba_and_grid_counts():
+    e = synth.ba(2000, 5, synth.stream(3))
+    assert len(e) == 5 * 6 // 2 + (2000 - 6) * 5 and len(np.unique(_keys(e))) == len(e)
+    g = synth.grid(50, 40, synth.stream(4))
+    assert len(g) == 2 * 50 * 49 + 40 and len(np.unique(_keys(g))) == len(g)
+
+
+def test_dyn_streams():
+    e = synth.er(500, 2000, synth.stream(5))
+    d = synth.DynGraph(500, e)
+    cur = set(_keys(e).tolist())
+    for law in (synth.UNIFORM, synth.PREFERENTIAL):
+        ins = d.sample_insert(300, law, synth.stream(5, 0, law, synth.INSERT))
+        k = _keys(ins)
+        assert len(ins) == 300 and len(set(k.tolist())) == 300 and not (set(k.tolist()) & cur)
+        dl = d.sample_delete(300, law, synth.stream(5, 0, law, synth.DELETE))
+        k = _keys(dl)
+        assert len(set(k.tolist())) == 300 and set(k.tolist()) <= cur
+    assert d.apply(0, ins) == 300 and d.m == 2300
+    nb = d.add_vertices(4, 6, synth.stream(5, 0, 0, synth.VINSERT))
+    assert d.n == 504 and nb.shape == (4, 6) and nb.max() < 500
+    dead = d.delete_vertices(3, synth.stream(5, 0, 0, synth.VDELETE))
+    al = d.alive()
+    assert (~al[dead]).all() and all(d.degree(int(v)) == 0 for v in dead)
