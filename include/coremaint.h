@@ -1,0 +1,228 @@
+/*
+ * coremaint.h -- C ABI of the GB300 (sm_103a) core-maintenance library.
+ *
+ * Method: batched incremental and decremental k-core maintenance by
+ * superior edge sets (N. Wang, D. Yu, H. Jin, C. Qian, X. Xie, Q.-S. Hua,
+ * "Parallel Algorithms for Core Maintenance in Dynamic Graphs",
+ * arXiv 1612.09368).  Core number: Section III, Definitions 1-2.  Superior
+ * edge / k-superior edge set / superior edge set: Section IV, Definition 6
+ * and the paragraph after it.  Incremental problem: Section III, Definition
+ * 4 and Section V (Algorithms 1-4).  Decremental problem: Definition 5 and
+ * Section VI (Algorithms 5-7).  Vertex insertion and deletion reduced to
+ * edge operations: Section I.
+ *
+ * General conventions
+ *  - Graphs are undirected and simple.  Vertex ids are dense int32 in
+ *    [0, n_total); new vertices get appended ids that are never reused.
+ *  - An edge list is an int32 array of 2*k entries (u0, v0, u1, v1, ...).
+ *    The order inside a pair does not matter; repeats collapse to one
+ *    (the first occurrence); self-loops are dropped; inserting an edge that
+ *    is present, or deleting one that is absent, is skipped and not an
+ *    error.  n_applied (nullable) reports how many edges were applied.
+ *  - Every pointer argument named "host or device" may be either: the
+ *    library detects device memory (cudaPointerGetAttributes) and copies
+ *    host memory in.  The caller owns its buffers; the library reads them
+ *    before the call returns and keeps no reference.  The library owns all
+ *    graph state in device memory.
+ *  - Calls run on the handle's CUDA stream and return after the work has
+ *    completed (synchronous semantics).  One handle must not be used from
+ *    two threads at once; distinct handles are independent.
+ *  - Return value: CM_OK (0) or a negative CM_ERR_* code.  Validation
+ *    happens before any mutation, so CM_ERR_INVALID and CM_ERR_OOM leave
+ *    the graph unchanged.  CM_ERR_CUDA and CM_ERR_LIMIT (a device wait or
+ *    iteration limit ran out) poison the handle: every later call except
+ *    cm_destroy / cm_last_error returns CM_ERR_STATE.
+ *  - cm_last_error() describes the most recent failure of a handle.
+ */
+#ifndef COREMAINT_H
+#define COREMAINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CM_OK 0
+#define CM_ERR_INVALID (-1)   /* bad argument: id out of range, dead vertex, NULL, negative size */
+#define CM_ERR_OOM (-2)       /* device or host allocation failed; graph unchanged */
+#define CM_ERR_CAPACITY (-3)  /* a size exceeds a documented maximum; graph unchanged */
+#define CM_ERR_LIMIT (-4)     /* a bounded device wait or iteration cap ran out; handle poisoned */
+#define CM_ERR_CUDA (-5)      /* a CUDA runtime call failed; handle poisoned */
+#define CM_ERR_STATE (-6)     /* handle poisoned by an earlier failure, or cores stale */
+
+#define CM_OP_INSERT 0
+#define CM_OP_DELETE 1
+
+typedef struct cm_graph cm_graph;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` bytes usable on `stream`,
+ * or NULL; free releases it.  When both are NULL the library uses
+ * cudaMalloc / cudaFree. */
+typedef void* (*cm_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*cm_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct cm_options {
+    int32_t slack_pct;      /* per-vertex adjacency headroom in percent (default 25) */
+    int32_t min_cap;        /* minimum adjacency slots per vertex, rounded up to 4 (default 4) */
+    int32_t block_threads;  /* threads per block of the persistent kernels (default 512) */
+    int32_t blocks_per_sm;  /* resident blocks per SM of the persistent kernels; 0 = occupancy limit */
+    int32_t max_sms;        /* SMs the persistent kernels may fill; 0 = all (lower it to share the GPU) */
+    int32_t reserved0;
+    int64_t spin_limit_ns;  /* limit of every grid-barrier wait (default 4e9 ns); CM_ERR_LIMIT past it */
+    cm_alloc_fn alloc;      /* optional allocator, see above */
+    cm_free_fn free;
+    void* alloc_ctx;
+    int32_t debug_flags;    /* test hooks, 0 in production (CM_DEBUG_*) */
+    int32_t reserved1;
+} cm_options;
+
+/* Test hook: every grid barrier of the next maintenance launch waits for
+ * one more block than exists, so each wait runs out after spin_limit_ns and
+ * the call returns CM_ERR_LIMIT (no fault, no hang). */
+#define CM_DEBUG_BARRIER_NEVER_RELEASES 1
+
+/* Counters of the most recent update call (or of cm_recompute_cores). */
+typedef struct cm_stats {
+    int64_t applied;         /* edges applied by the call */
+    int64_t iterations;      /* superior-edge-set iterations (Algorithm 1 / 5 while-loop) */
+    int64_t select_rounds;   /* claim rounds summed over iterations */
+    int64_t selected;        /* edges selected, summed over iterations (= applied) */
+    int64_t remaining_sum;   /* remaining edges at iteration start, summed */
+    int64_t visited;         /* vertices entered into the candidate set (insert) */
+    int64_t visited_slots;   /* adjacency slots of those vertices */
+    int64_t evicted;         /* vertices evicted by support waves */
+    int64_t evicted_slots;
+    int64_t changed;         /* vertices whose core moved by one */
+    int64_t changed_slots;
+    int64_t waves;           /* discovery + eviction waves */
+    int64_t alg_bytes;       /* algorithmic HBM bytes of the maintenance kernel (see design notes) */
+    int64_t launches;        /* kernels this library launched during the call */
+    double maintain_ms;      /* device time of the maintenance kernel (CUDA events on the handle's stream) */
+    double call_ms;          /* device time of the whole call, first copy to last kernel */
+    int64_t peel_levels;     /* cm_recompute_cores / cm_create: peeling levels */
+    int64_t reserved[7];
+} cm_stats;
+
+/* Fills *opt with the defaults. */
+void cm_default_options(cm_options* opt);
+
+/* Creates a graph with n vertices (ids 0..n-1) from m undirected edges
+ * (host or device, 2*m int32).  cores (host or device, n int32, nullable):
+ * the exact core numbers of this graph, the input of Algorithms 1 and 5;
+ * when NULL they are computed on the GPU by bucket peeling (the static
+ * decomposition the paper cites as [O(m)]).  Passing wrong cores gives
+ * wrong maintenance results; they are not verified.  stream: a
+ * cudaStream_t (NULL = legacy default stream) on which every later call of
+ * this handle runs.  Repeated edges and self-loops in the list are dropped.
+ * Errors: CM_ERR_INVALID (out, n < 0, m < 0, id out of range), CM_ERR_OOM,
+ * CM_ERR_CUDA. */
+int cm_create(cm_graph** out, int32_t n, const int32_t* edges, int64_t m, const int32_t* cores,
+              const cm_options* opt, void* stream);
+
+/* Frees the handle and all its device memory.  NULL is ignored. */
+void cm_destroy(cm_graph* g);
+
+/* Incremental core maintenance (Algorithm 1): inserts the k edges
+ * (host or device, 2*k int32) and updates every core number.  Each
+ * iteration selects a maximal superior edge set from the remaining edges
+ * (Algorithm 2 with a fixed priority), inserts it, finds per core level the
+ * vertices whose core rises (Algorithms 3-4) and raises them by one.
+ * Errors: CM_ERR_INVALID (an id out of range or dead; nothing applied). */
+int cm_insert_edges(cm_graph* g, const int32_t* edges, int64_t k, int64_t* n_applied);
+
+/* Decremental core maintenance (Algorithm 5, with Algorithms 6-7): deletes
+ * the k edges and updates every core number.  Errors as cm_insert_edges. */
+int cm_delete_edges(cm_graph* g, const int32_t* edges, int64_t k, int64_t* n_applied);
+
+/* Vertex insertion (Section I): appends `count` vertices with ids
+ * n_total .. n_total+count-1 and core 0, then inserts their edges as one
+ * batch.  Vertex i's neighbours are nbrs[nbr_off[i] .. nbr_off[i+1]);
+ * nbr_off (count+1 int64) and nbrs may be host or device.  A neighbour may
+ * be a live existing vertex or another vertex of this call, but not the
+ * vertex itself.  *first_id (nullable) receives n_total before the call.
+ * Errors: CM_ERR_INVALID (bad neighbour, self-loop), CM_ERR_OOM. */
+int cm_insert_vertices(cm_graph* g, int32_t count, const int64_t* nbr_off, const int32_t* nbrs,
+                       int32_t* first_id, int64_t* n_applied);
+
+/* One vertex with d neighbours; *new_id receives its id. */
+int cm_insert_vertex(cm_graph* g, const int32_t* nbrs, int32_t d, int32_t* new_id);
+
+/* Vertex deletion (Section I): deletes every edge incident to the given
+ * live vertices (host or device, count int32; repeats allowed) as one
+ * batch, then marks them dead: they keep their ids, report core -1 and
+ * reject later edges.  n_applied: edges deleted.  Errors: CM_ERR_INVALID
+ * (id out of range or already dead; nothing changed). */
+int cm_delete_vertices(cm_graph* g, int32_t count, const int32_t* ids, int64_t* n_applied);
+
+/* One vertex. */
+int cm_delete_vertex(cm_graph* g, int32_t v);
+
+/* Copies the core number of every vertex (n_total int32, dead = -1) into
+ * out (host or device; NULL only queries the size).  *n_total (nullable)
+ * receives the vertex count.  CM_ERR_STATE if cores are stale (after
+ * cm_apply_edges without cm_recompute_cores). */
+int cm_get_cores(const cm_graph* g, int32_t* out, int32_t* n_total);
+
+/* Copies the current edge list (canonical pairs lo < hi, any order) into
+ * host or device memory of capacity cap pairs; *m receives the edge count.
+ * With cm_get_cores this is a complete checkpoint: cm_create(edges, cores)
+ * resumes it.  CM_ERR_CAPACITY (nothing copied) when cap < m. */
+int cm_get_edges(const cm_graph* g, int32_t* out, int64_t cap, int64_t* m);
+
+/* Vertex count (including dead ids) and live edge count. */
+int32_t cm_num_vertices(const cm_graph* g);
+int64_t cm_num_edges(const cm_graph* g);
+
+/* Applies an edge batch to the graph structure only (op CM_OP_INSERT or
+ * CM_OP_DELETE), leaving core numbers stale until cm_recompute_cores.
+ * Together they form the full re-peel comparator: the alternative to
+ * maintenance that the paper argues against (Section I). */
+int cm_apply_edges(cm_graph* g, int32_t op, const int32_t* edges, int64_t k, int64_t* n_applied);
+
+/* Recomputes every core number from scratch by GPU bucket peeling (the
+ * [O(m)] decomposition the paper cites, level-synchronous) and rebuilds
+ * the per-vertex superior degrees. */
+int cm_recompute_cores(cm_graph* g);
+
+/* Counters of the most recent call. */
+int cm_get_stats(const cm_graph* g, cm_stats* out);
+
+/* Changes the stream of the handle (cudaStream_t). */
+int cm_set_stream(cm_graph* g, void* stream);
+
+/* Description of the most recent failure of g (or of the last failed
+ * cm_create when g is NULL); never NULL. */
+const char* cm_last_error(const cm_graph* g);
+
+/* ---------------- many independent graphs in one handle ----------------
+ * A multi-graph handle stores `ngraphs` independent graphs as one disjoint
+ * union: local vertex v of graph i has global id base[i] + v.  Because no
+ * edge joins two graphs, one maintenance launch serves every graph's batch
+ * at once and each graph's core numbers are exactly those of the graph on
+ * its own. */
+
+/* ns[i]: vertex count of graph i; ms[i]: its edge count; edges: the graphs'
+ * edge lists (local ids) concatenated in graph order (host or device);
+ * cores: NULL (peel) or the concatenated core numbers.  ns and ms are host
+ * arrays. */
+int cm_create_multi(cm_graph** out, int32_t ngraphs, const int32_t* ns, const int64_t* ms,
+                    const int32_t* edges, const int32_t* cores, const cm_options* opt, void* stream);
+
+/* Number of graphs and the base id of each (host array of ngraphs). */
+int cm_multi_bases(const cm_graph* g, int32_t* bases, int32_t* ngraphs);
+
+/* One insert or delete batch per graph, run as a single fused call:
+ * counts[i] (host) edges of graph i, local ids, concatenated in graph order
+ * (host or device).  n_applied (host, nullable, ngraphs entries) receives
+ * per-graph applied counts. */
+int cm_update_multi(cm_graph* g, int32_t op, const int64_t* counts, const int32_t* edges,
+                    int64_t* n_applied);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COREMAINT_H */

@@ -22,7 +22,7 @@
  *                  DeleteRemove (Section VI, Algorithms 6-7) with |E_k| = 1.
  *   O4  mode 1     the batched method: SuperiorEdgeInsert (Algorithm 1) and
  *                  SuperiorEdgeDelete (Algorithm 5), each iteration selecting
- *                  a superior edge set (Section IV Def. 3 and the union that
+ *                  a superior edge set (Section IV Definition 6 and the union that
  *                  follows it; Algorithm 2), running Algorithm 3/6 once per
  *                  core level on the cores of the iteration's start, then
  *                  moving every found vertex by one.
@@ -34,7 +34,7 @@
  *     bijection, so priorities are distinct.  Each iteration takes, in
  *     increasing priority, every remaining edge none of whose constrained
  *     endpoints (endpoints whose core equals the edge's core number,
- *     Section IV) is already taken.  The result satisfies Def. 3 (ii) at
+ *     Section IV) is already taken.  The result satisfies Definition 6 (ii) at
  *     every level and is maximal.
  *  R2 The level set C of Algorithm 1 is recomputed from the remaining edges
  *     at the start of every iteration, as Algorithm 5 does explicitly.
@@ -318,7 +318,7 @@ static void reset_scratch(or_graph* g) {
     g->ntl = 0;
 }
 
-/* SD(u), Def. 4: the number of neighbours w with core(w) >= core(u). */
+/* SD(u), Definition 7 (superior degree): the number of neighbours w with core(w) >= core(u). */
 static int32_t SD(or_graph* g, int32_t u) {
     if (g->sdok[u]) return g->sdv[u];
     int32_t c = 0;
@@ -327,7 +327,7 @@ static int32_t SD(or_graph* g, int32_t u) {
     g->sdv[u] = c; g->sdok[u] = 1;
     return c;
 }
-/* CSD(u), Def. 5: neighbours w with core(w) > core(u), or core(w) = core(u)
+/* CSD(u), Definition 8 (constraint superior degree): neighbours w with core(w) > core(u), or core(w) = core(u)
  * and SD(w) > core(u). */
 static int32_t CSD(or_graph* g, int32_t u) {
     int32_t c = 0, k = g->core[u];

@@ -1,0 +1,423 @@
+"""GB300-native batched k-core maintenance by superior edge sets.
+
+Thin Python binding over the C ABI declared in include/coremaint.h
+(libcoremaint.so, built by ``build.build()``).  Every function here only
+marshals arguments -- numpy arrays, torch tensors (CPU or CUDA) and streams
+-- into the C calls of the same name; all graph work runs in the library's
+CUDA kernels.  Importing fails loudly when the library is missing.
+
+Method: N. Wang et al., "Parallel Algorithms for Core Maintenance in Dynamic
+Graphs" (arXiv 1612.09368): superior edge sets (Section IV), incremental
+maintenance (Section V, Algorithms 1-4), decremental maintenance (Section VI,
+Algorithms 5-7), vertex operations reduced to edge operations (Section I).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "CM_OK", "CM_ERR_INVALID", "CM_ERR_OOM", "CM_ERR_CAPACITY", "CM_ERR_LIMIT", "CM_ERR_CUDA", "CM_ERR_STATE",
+    "CM_OP_INSERT", "CM_OP_DELETE", "CM_DEBUG_BARRIER_NEVER_RELEASES", "CoreMaintError", "cm_options", "cm_stats",
+    "lib", "library_path", "cm_default_options", "cm_create", "cm_create_multi", "cm_destroy", "cm_insert_edges",
+    "cm_delete_edges", "cm_insert_vertices", "cm_insert_vertex", "cm_delete_vertices", "cm_delete_vertex",
+    "cm_get_cores", "cm_get_edges", "cm_num_vertices", "cm_num_edges", "cm_apply_edges", "cm_recompute_cores",
+    "cm_get_stats", "cm_set_stream", "cm_last_error", "cm_multi_bases", "cm_update_multi", "CoreGraph",
+]
+
+CM_OK = 0
+CM_ERR_INVALID = -1
+CM_ERR_OOM = -2
+CM_ERR_CAPACITY = -3
+CM_ERR_LIMIT = -4
+CM_ERR_CUDA = -5
+CM_ERR_STATE = -6
+CM_OP_INSERT = 0
+CM_OP_DELETE = 1
+CM_DEBUG_BARRIER_NEVER_RELEASES = 1
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class cm_options(ctypes.Structure):
+    _fields_ = [
+        ("slack_pct", ctypes.c_int32), ("min_cap", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32), ("max_sms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("spin_limit_ns", ctypes.c_int64), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+        ("debug_flags", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+    ]
+
+
+class cm_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "applied", "iterations", "select_rounds", "selected", "remaining_sum", "visited", "visited_slots",
+        "evicted", "evicted_slots", "changed", "changed_slots", "waves", "alg_bytes", "launches")] + [
+        ("maintain_ms", ctypes.c_double), ("call_ms", ctypes.c_double), ("peel_levels", ctypes.c_int64),
+        ("reserved", ctypes.c_int64 * 7)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class CoreMaintError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+library_path = _build.LIB
+
+
+def lib():
+    """The loaded libcoremaint.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise ImportError(f"{library_path} is missing: run paper_1612_09368_gb300.build.build() "
+                              "(needs nvcc); there is no CPU fallback")
+        L = ctypes.CDLL(library_path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        p32 = ctypes.POINTER(ctypes.c_int32)
+        p64 = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "cm_default_options": (None, [ctypes.POINTER(cm_options)]),
+            "cm_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, vp, i64, vp, ctypes.POINTER(cm_options), vp]),
+            "cm_create_multi": (ctypes.c_int, [ctypes.POINTER(vp), i32, p32, p64, vp, vp,
+                                               ctypes.POINTER(cm_options), vp]),
+            "cm_destroy": (None, [vp]),
+            "cm_insert_edges": (ctypes.c_int, [vp, vp, i64, p64]),
+            "cm_delete_edges": (ctypes.c_int, [vp, vp, i64, p64]),
+            "cm_insert_vertices": (ctypes.c_int, [vp, i32, vp, vp, p32, p64]),
+            "cm_insert_vertex": (ctypes.c_int, [vp, vp, i32, p32]),
+            "cm_delete_vertices": (ctypes.c_int, [vp, i32, vp, p64]),
+            "cm_delete_vertex": (ctypes.c_int, [vp, i32]),
+            "cm_get_cores": (ctypes.c_int, [vp, vp, p32]),
+            "cm_get_edges": (ctypes.c_int, [vp, vp, i64, p64]),
+            "cm_num_vertices": (i32, [vp]),
+            "cm_num_edges": (i64, [vp]),
+            "cm_apply_edges": (ctypes.c_int, [vp, i32, vp, i64, p64]),
+            "cm_recompute_cores": (ctypes.c_int, [vp]),
+            "cm_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(cm_stats)]),
+            "cm_set_stream": (ctypes.c_int, [vp, vp]),
+            "cm_last_error": (ctypes.c_char_p, [vp]),
+            "cm_multi_bases": (ctypes.c_int, [vp, p32, p32]),
+            "cm_update_multi": (ctypes.c_int, [vp, i32, p64, vp, p64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- marshalling
+def _arr(x, dtype):
+    """(pointer, keepalive) for a host numpy array or a torch tensor."""
+    if x is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            tdt = torch.int32 if dtype == np.int32 else torch.int64
+            t = x.to(tdt).contiguous()
+            return ctypes.c_void_p(t.data_ptr()), t
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(h, rc, what):
+    if rc != CM_OK:
+        msg = lib().cm_last_error(h)
+        raise CoreMaintError(rc, f"{what}: {msg.decode() if msg else ''}")
+    return rc
+
+
+def _npairs(x) -> int:
+    shape = getattr(x, "shape", None)
+    if shape is not None and len(shape) == 2:
+        return int(shape[0])
+    return len(x) // 2 if not hasattr(x, "numel") else int(x.numel()) // 2
+
+
+# Device allocation through torch's caching allocator.
+class _TorchAllocator:
+    def __init__(self):
+        import torch
+        self._torch = torch
+
+        def _alloc(size, stream, ctx):
+            try:
+                return int(self._torch.cuda.caching_allocator_alloc(int(size), stream=int(stream or 0)))
+            except Exception:
+                return None
+
+        def _free(ptr, size, stream, ctx):
+            self._torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = _ALLOC_FN(_alloc)
+        self.free = _FREE_FN(_free)
+
+
+# ---------------------------------------------------------------- C-named functions
+def cm_default_options() -> cm_options:
+    o = cm_options()
+    lib().cm_default_options(ctypes.byref(o))
+    return o
+
+
+def cm_create(n, edges, cores=None, options: cm_options | None = None, stream=None):
+    h = ctypes.c_void_p()
+    ep, ek = _arr(edges, np.int32)
+    cp, ck = _arr(cores, np.int32)
+    m = _npairs(edges) if edges is not None else 0
+    rc = lib().cm_create(ctypes.byref(h), int(n), ep, m, cp, ctypes.byref(options) if options else None,
+                         _stream(stream))
+    _check(None, rc, "cm_create")
+    return h
+
+
+def cm_create_multi(ns, ms, edges, cores=None, options: cm_options | None = None, stream=None):
+    h = ctypes.c_void_p()
+    nsa = np.ascontiguousarray(ns, dtype=np.int32)
+    msa = np.ascontiguousarray(ms, dtype=np.int64)
+    ep, ek = _arr(edges, np.int32)
+    cp, ck = _arr(cores, np.int32)
+    rc = lib().cm_create_multi(ctypes.byref(h), len(nsa), nsa.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               msa.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ep, cp,
+                               ctypes.byref(options) if options else None, _stream(stream))
+    _check(None, rc, "cm_create_multi")
+    return h
+
+
+def cm_destroy(h):
+    lib().cm_destroy(h)
+
+
+def _upd(fn, h, edges, what):
+    ep, keep = _arr(edges, np.int32)
+    applied = ctypes.c_int64(0)
+    _check(h, fn(h, ep, _npairs(edges), ctypes.byref(applied)), what)
+    return applied.value
+
+
+def cm_insert_edges(h, edges) -> int:
+    return _upd(lib().cm_insert_edges, h, edges, "cm_insert_edges")
+
+
+def cm_delete_edges(h, edges) -> int:
+    return _upd(lib().cm_delete_edges, h, edges, "cm_delete_edges")
+
+
+def cm_apply_edges(h, op, edges) -> int:
+    ep, keep = _arr(edges, np.int32)
+    applied = ctypes.c_int64(0)
+    _check(h, lib().cm_apply_edges(h, int(op), ep, _npairs(edges), ctypes.byref(applied)), "cm_apply_edges")
+    return applied.value
+
+
+def cm_insert_vertices(h, nbr_off, nbrs):
+    """Returns (first new id, edges applied)."""
+    op, ok = _arr(nbr_off, np.int64)
+    npt, nk = _arr(nbrs, np.int32)
+    count = (len(nbr_off) if not hasattr(nbr_off, "numel") else int(nbr_off.numel())) - 1
+    first = ctypes.c_int32(0)
+    applied = ctypes.c_int64(0)
+    _check(h, lib().cm_insert_vertices(h, count, op, npt, ctypes.byref(first), ctypes.byref(applied)),
+           "cm_insert_vertices")
+    return first.value, applied.value
+
+
+def cm_insert_vertex(h, nbrs) -> int:
+    npt, nk = _arr(nbrs, np.int32)
+    d = len(nbrs) if not hasattr(nbrs, "numel") else int(nbrs.numel())
+    vid = ctypes.c_int32(0)
+    _check(h, lib().cm_insert_vertex(h, npt, d, ctypes.byref(vid)), "cm_insert_vertex")
+    return vid.value
+
+
+def cm_delete_vertices(h, ids) -> int:
+    ip, ik = _arr(ids, np.int32)
+    count = len(ids) if not hasattr(ids, "numel") else int(ids.numel())
+    applied = ctypes.c_int64(0)
+    _check(h, lib().cm_delete_vertices(h, count, ip, ctypes.byref(applied)), "cm_delete_vertices")
+    return applied.value
+
+
+def cm_delete_vertex(h, v: int):
+    _check(h, lib().cm_delete_vertex(h, int(v)), "cm_delete_vertex")
+
+
+def cm_num_vertices(h) -> int:
+    return int(lib().cm_num_vertices(h))
+
+
+def cm_num_edges(h) -> int:
+    return int(lib().cm_num_edges(h))
+
+
+def cm_get_cores(h, out=None):
+    """Core numbers (dead vertices -1) into `out` (a torch tensor, host or
+    CUDA) or a new numpy array."""
+    n = cm_num_vertices(h)
+    if out is None:
+        out = np.empty(n, dtype=np.int32)
+        _check(h, lib().cm_get_cores(h, ctypes.c_void_p(out.ctypes.data), None), "cm_get_cores")
+        return out
+    _check(h, lib().cm_get_cores(h, ctypes.c_void_p(out.data_ptr()), None), "cm_get_cores")
+    return out
+
+
+def cm_get_edges(h) -> np.ndarray:
+    m = cm_num_edges(h)
+    out = np.empty((max(m, 0), 2), dtype=np.int32)
+    got = ctypes.c_int64(0)
+    _check(h, lib().cm_get_edges(h, ctypes.c_void_p(out.ctypes.data), m, ctypes.byref(got)), "cm_get_edges")
+    return out
+
+
+def cm_recompute_cores(h):
+    _check(h, lib().cm_recompute_cores(h), "cm_recompute_cores")
+
+
+def cm_get_stats(h) -> dict:
+    s = cm_stats()
+    _check(h, lib().cm_get_stats(h, ctypes.byref(s)), "cm_get_stats")
+    return s.as_dict()
+
+
+def cm_set_stream(h, stream):
+    _check(h, lib().cm_set_stream(h, _stream(stream)), "cm_set_stream")
+
+
+def cm_last_error(h) -> str:
+    m = lib().cm_last_error(h)
+    return m.decode() if m else ""
+
+
+def cm_multi_bases(h) -> np.ndarray:
+    ng = ctypes.c_int32(0)
+    lib().cm_multi_bases(h, None, ctypes.byref(ng))
+    out = np.empty(ng.value, dtype=np.int32)
+    lib().cm_multi_bases(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(ng))
+    return out
+
+
+def cm_update_multi(h, op, counts, edges) -> np.ndarray:
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    ep, ek = _arr(edges, np.int32)
+    out = np.zeros(len(c), dtype=np.int64)
+    _check(h, lib().cm_update_multi(h, int(op), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ep,
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "cm_update_multi")
+    return out
+
+
+# ---------------------------------------------------------------- convenience object
+class CoreGraph:
+    """Owning wrapper: a graph resident on the GPU with maintained cores."""
+
+    def __init__(self, n, edges, cores=None, *, stream=None, use_torch_allocator=True, multi=None, **opts):
+        o = cm_default_options()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self._alloc = None
+        if use_torch_allocator:
+            self._alloc = _TorchAllocator()
+            o.alloc = self._alloc.alloc
+            o.free = self._alloc.free
+        self.options = o
+        self._stream = stream
+        if multi is not None:
+            ns, ms = multi
+            self._h = cm_create_multi(ns, ms, edges, cores, o, stream)
+        else:
+            self._h = cm_create(n, edges, cores, o, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            cm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def n(self) -> int:
+        return cm_num_vertices(self._h)
+
+    @property
+    def m(self) -> int:
+        return cm_num_edges(self._h)
+
+    def insert_edges(self, edges) -> int:
+        return cm_insert_edges(self._h, edges)
+
+    def delete_edges(self, edges) -> int:
+        return cm_delete_edges(self._h, edges)
+
+    def apply_edges(self, op, edges) -> int:
+        return cm_apply_edges(self._h, op, edges)
+
+    def insert_vertices(self, nbr_lists):
+        lens = [len(x) for x in nbr_lists]
+        off = np.zeros(len(lens) + 1, dtype=np.int64)
+        off[1:] = np.cumsum(lens)
+        nb = (np.concatenate([np.asarray(x, dtype=np.int32) for x in nbr_lists]) if off[-1]
+              else np.zeros(0, dtype=np.int32))
+        return cm_insert_vertices(self._h, off, nb)
+
+    def delete_vertices(self, ids) -> int:
+        return cm_delete_vertices(self._h, ids)
+
+    def cores(self, out=None):
+        return cm_get_cores(self._h, out)
+
+    def edges(self) -> np.ndarray:
+        return cm_get_edges(self._h)
+
+    def recompute_cores(self):
+        cm_recompute_cores(self._h)
+
+    def stats(self) -> dict:
+        return cm_get_stats(self._h)
+
+    def bases(self) -> np.ndarray:
+        return cm_multi_bases(self._h)
+
+    def update_multi(self, op, counts, edges) -> np.ndarray:
+        return cm_update_multi(self._h, op, counts, edges)

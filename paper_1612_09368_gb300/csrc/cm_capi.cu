@@ -1,0 +1,1027 @@
+// cm_capi.cu -- host implementation of the C ABI in include/coremaint.h.
+//
+// A handle owns one graph (or a disjoint union of many) in device memory
+// and runs every call on its stream.  An update call is:
+//   copy batch in -> ingest (validate, canonicalise, dedupe, filter against
+//   the edge index) -> read back counts -> relocate vertices whose slack the
+//   batch exceeds -> one cooperative launch of the maintenance kernel, which
+//   runs all superior-edge-set iterations -> read back status and counters.
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/coremaint.h"
+#include "cm_common.cuh"
+#include "cm_launch.h"
+
+using namespace cm;
+
+static thread_local std::string g_create_err = "no error";
+
+struct cm_graph {
+    cm_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int32_t n = 0, ncap = 0;
+    int64_t m = 0;
+    unsigned long long idx_size = 0;
+    int64_t idx_live = 0, idx_tomb = 0;
+    uint32_t epoch = 1;
+    bool poisoned = false, cores_stale = false;
+    std::string err = "no error";
+    DevGraph g{};
+    Ctl* ctl = nullptr;
+    Ctl* hctl = nullptr;   // pinned mirror
+    // batch buffers
+    int32_t* dbatch = nullptr;
+    long long batch_cap = 0;  // pairs
+    BSet* bset = nullptr;
+    unsigned long long bset_size = 0;
+    REdge* R0 = nullptr;
+    REdge* R1 = nullptr;
+    long long rcap = 0;
+    // per-vertex scratch rings (also the peel's scratch)
+    int32_t* VQ = nullptr;
+    int32_t* EQ = nullptr;
+    int32_t* CQ = nullptr;
+    int32_t* OVL = nullptr;
+    unsigned long long qmask = 0;
+    // multi-graph (small arrays, plain cudaMalloc)
+    int32_t ngraphs = 1;
+    std::vector<int32_t> bases;
+    int32_t* dbases = nullptr;
+    long long* dprefix = nullptr;
+    unsigned long long* dpergraph = nullptr;
+    // timing and counters
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cm_stats last{};
+    long long launches = 0;
+};
+
+// ------------------------------------------------------------------ helpers
+static int set_err(cm_graph* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_err = buf;
+    return code;
+}
+
+static int fail_cuda(cm_graph* h, cudaError_t e, const char* what) {
+    if (h) h->poisoned = true;
+    return set_err(h, CM_ERR_CUDA, "CUDA error in %s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, x)                                            \
+    do {                                                    \
+        cudaError_t _e = (x);                               \
+        if (_e != cudaSuccess) return fail_cuda(h, _e, #x); \
+    } while (0)
+
+#define LAUNCH(h, x)     \
+    do {                 \
+        (h)->launches++; \
+        CK(h, x);        \
+    } while (0)
+
+static void* dalloc(cm_graph* h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (h->opt.alloc) return h->opt.alloc(bytes, (void*)h->stream, h->opt.alloc_ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+static void dfree(cm_graph* h, void* p, size_t bytes) {
+    if (!p) return;
+    if (h->opt.free) h->opt.free(p, bytes ? bytes : 16, (void*)h->stream, h->opt.alloc_ctx);
+    else cudaFree(p);
+}
+
+template <class T>
+static bool realloc_dev(cm_graph* h, T*& p, size_t old_elems, size_t new_elems, size_t keep_elems) {
+    T* q = (T*)dalloc(h, new_elems * sizeof(T));
+    if (!q) return false;
+    if (p && keep_elems) {
+        if (cudaMemcpyAsync(q, p, keep_elems * sizeof(T), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) {
+            dfree(h, q, new_elems * sizeof(T));
+            return false;
+        }
+    }
+    if (p) {
+        cudaStreamSynchronize(h->stream);
+        dfree(h, p, old_elems * sizeof(T));
+    }
+    p = q;
+    return true;
+}
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static unsigned long long pow2_at_least(unsigned long long x) {
+    unsigned long long p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+static int rd_ctl(cm_graph* h) {
+    CK(h, cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return CM_OK;
+}
+
+// Reset the fields a persistent launch uses (barrier, tails, counters, stats).
+static int reset_launch_zone(cm_graph* h) {
+    CK(h, cudaMemsetAsync(h->ctl, 0, offsetof(Ctl, nrem), h->stream));
+    return CM_OK;
+}
+
+// Reset the host-exchange words; adj_top stays (it is device-owned).
+static int reset_ingest_zone(cm_graph* h) {
+    CK(h, cudaMemsetAsync(&h->ctl->error, 0, sizeof(int) * 2, h->stream));
+    CK(h, cudaMemsetAsync(&h->ctl->nrem, 0, sizeof(unsigned long long) * 3, h->stream));
+    CK(h, cudaMemsetAsync(&h->ctl->bad_index, 0x7F, sizeof(long long), h->stream));   // large positive
+    CK(h, cudaMemsetAsync(&h->ctl->gather_n, 0, sizeof(unsigned long long), h->stream));
+    return CM_OK;
+}
+
+// ------------------------------------------------------------------ capacity management
+static int grow_vertices(cm_graph* h, int32_t need) {
+    if (need <= h->ncap) return CM_OK;
+    long long nc = (long long)need + need / 4 + 1024;
+    if (nc > INT32_MAX) nc = INT32_MAX;
+    int32_t keep = h->n;
+    DevGraph& g = h->g;
+    size_t oc = (size_t)h->ncap;
+    bool ok = realloc_dev(h, g.hs, oc, nc, keep) && realloc_dev(h, g.off, oc, nc, keep) &&
+              realloc_dev(h, g.end, oc, nc, keep) && realloc_dev(h, g.cap, oc, nc, keep) &&
+              realloc_dev(h, g.deg, oc, nc, keep) && realloc_dev(h, g.chg, oc, nc, keep) &&
+              realloc_dev(h, g.taken, oc, nc, keep) && realloc_dev(h, g.claim0, oc, nc, keep) &&
+              realloc_dev(h, g.claim1, oc, nc, keep) && realloc_dev(h, g.need, oc, nc, keep);
+    if (!ok) return set_err(h, CM_ERR_OOM, "out of device memory growing vertex arrays to %lld", nc);
+    size_t tail = (size_t)(nc - keep);
+    CK(h, cudaMemsetAsync(g.hs + keep, 0, tail * sizeof(int4), h->stream));
+    CK(h, cudaMemsetAsync(g.end + keep, 0, tail * sizeof(int32_t), h->stream));
+    CK(h, cudaMemsetAsync(g.cap + keep, 0, tail * sizeof(int32_t), h->stream));
+    CK(h, cudaMemsetAsync(g.deg + keep, 0, tail * sizeof(int32_t), h->stream));
+    CK(h, cudaMemsetAsync(g.off + keep, 0, tail * sizeof(int64_t), h->stream));
+    CK(h, cudaMemsetAsync(g.chg + keep, 0, tail * sizeof(uint32_t), h->stream));
+    CK(h, cudaMemsetAsync(g.taken + keep, 0, tail * sizeof(uint32_t), h->stream));
+    CK(h, cudaMemsetAsync(g.claim0 + keep, 0xFF, tail * sizeof(unsigned long long), h->stream));
+    CK(h, cudaMemsetAsync(g.claim1 + keep, 0xFF, tail * sizeof(unsigned long long), h->stream));
+    CK(h, cudaMemsetAsync(g.need + keep, 0, tail * sizeof(int32_t), h->stream));
+    unsigned long long qn = pow2_at_least((unsigned long long)nc);
+    size_t oq = h->qmask ? (size_t)(h->qmask + 1) : 0;
+    if (qn != oq) {
+        ok = realloc_dev(h, h->VQ, oq, qn, 0) && realloc_dev(h, h->EQ, oq, qn, 0) &&
+             realloc_dev(h, h->CQ, oq, qn, 0) && realloc_dev(h, h->OVL, oq, qn, 0);
+        if (!ok) return set_err(h, CM_ERR_OOM, "out of device memory for queues");
+        h->qmask = qn - 1;
+    }
+    h->ncap = (int32_t)nc;
+    return CM_OK;
+}
+
+// Make room for need_slots more adjacency slots after the pool top.
+static int grow_pool(cm_graph* h, long long need_slots) {
+    unsigned long long top = 0;
+    CK(h, cudaMemcpyAsync(&h->hctl->adj_top, &h->ctl->adj_top, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    top = h->hctl->adj_top;
+    if ((long long)top + need_slots <= h->g.adj_cap) return CM_OK;
+    long long nc = (long long)top + need_slots;
+    nc = nc + nc / 4 + 4096;
+    if (!realloc_dev(h, h->g.adj, (size_t)h->g.adj_cap, (size_t)nc, (size_t)top))
+        return set_err(h, CM_ERR_OOM, "out of device memory growing the adjacency pool to %lld slots", nc);
+    h->g.adj_cap = nc;
+    return CM_OK;
+}
+
+static int alloc_index(cm_graph* h, unsigned long long size) {
+    Bucket* p = (Bucket*)dalloc(h, size * sizeof(Bucket));
+    if (!p) return set_err(h, CM_ERR_OOM, "out of device memory for an edge index of %llu buckets", size);
+    CK(h, cudaMemsetAsync(p, 0xFF, size * sizeof(Bucket), h->stream));
+    h->g.idx = p;
+    h->g.idx_mask = size - 1;
+    h->idx_size = size;
+    return CM_OK;
+}
+
+// Grow or clean the index so that `adding` more keys keep its load <= 1/2.
+static int ensure_index(cm_graph* h, long long adding) {
+    long long used = h->idx_live + h->idx_tomb + adding;
+    if ((unsigned long long)used * 2 <= h->idx_size) return CM_OK;
+    long long want = (h->idx_live + adding) * 5 / 2 + 1024;
+    unsigned long long ns = pow2_at_least((unsigned long long)want);
+    if (ns < h->idx_size) ns = h->idx_size;
+    Bucket* old = h->g.idx;
+    unsigned long long old_size = h->idx_size;
+    int rc = alloc_index(h, ns);
+    if (rc) {
+        h->g.idx = old;
+        h->g.idx_mask = old_size - 1;
+        h->idx_size = old_size;
+        return rc;
+    }
+    LAUNCH(h, rehash(old, old_size, h->g, h->ctl, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    dfree(h, old, old_size * sizeof(Bucket));
+    h->idx_tomb = 0;
+    return CM_OK;
+}
+
+// Batch buffers for k edges: staging copy, dedupe set, remaining lists.
+static int ensure_batch(cm_graph* h, long long k) {
+    if (k > h->batch_cap) {
+        long long nc = k + k / 2 + 1024;
+        int32_t* q = (int32_t*)dalloc(h, (size_t)nc * 2 * sizeof(int32_t));
+        if (!q) return set_err(h, CM_ERR_OOM, "out of device memory for a batch of %lld edges", k);
+        dfree(h, h->dbatch, (size_t)h->batch_cap * 2 * sizeof(int32_t));
+        h->dbatch = q;
+        h->batch_cap = nc;
+    }
+    unsigned long long bs = pow2_at_least((unsigned long long)(2 * k + 16));
+    if (bs > h->bset_size) {
+        BSet* q = (BSet*)dalloc(h, bs * sizeof(BSet));
+        if (!q) return set_err(h, CM_ERR_OOM, "out of device memory for a batch set");
+        dfree(h, h->bset, h->bset_size * sizeof(BSet));
+        h->bset = q;
+        h->bset_size = bs;
+    }
+    if (k > h->rcap) {
+        long long nc = k + k / 2 + 1024;
+        REdge* a = (REdge*)dalloc(h, (size_t)nc * sizeof(REdge));
+        REdge* b = (REdge*)dalloc(h, (size_t)nc * sizeof(REdge));
+        if (!a || !b) {
+            dfree(h, a, (size_t)nc * sizeof(REdge));
+            dfree(h, b, (size_t)nc * sizeof(REdge));
+            return set_err(h, CM_ERR_OOM, "out of device memory for remaining-edge lists");
+        }
+        dfree(h, h->R0, (size_t)h->rcap * sizeof(REdge));
+        dfree(h, h->R1, (size_t)h->rcap * sizeof(REdge));
+        h->R0 = a;
+        h->R1 = b;
+        h->rcap = nc;
+    }
+    return CM_OK;
+}
+
+// ------------------------------------------------------------------ launch geometry
+// Persistent kernels fill max_sms SMs (all by default) with as many blocks
+// as stay resident.  A small batch gets fewer blocks: grid barriers then
+// cost less, and there is not enough work for the whole GPU anyway.
+static void persistent_geometry(cm_graph* h, int kind, long long work, int* blocks, int* threads) {
+    int t = h->opt.block_threads > 0 ? h->opt.block_threads : 512;
+    int occ = kind == 0 ? maintain_blocks_per_sm(t) : peel_blocks_per_sm(t);
+    if (occ < 1) occ = 1;
+    int bps = h->opt.blocks_per_sm > 0 ? (h->opt.blocks_per_sm < occ ? h->opt.blocks_per_sm : occ) : occ;
+    int sms = h->opt.max_sms > 0 && h->opt.max_sms < h->num_sms ? h->opt.max_sms : h->num_sms;
+    long long b = (long long)sms * bps;
+    if (kind == 0 && h->opt.blocks_per_sm <= 0) {
+        long long want = (work * 64 + t - 1) / t;
+        if (want < sms) want = sms;
+        if (want < b) b = want;
+    }
+    if (b < 1) b = 1;
+    *blocks = (int)b;
+    *threads = t;
+}
+
+// ------------------------------------------------------------------ create / destroy
+extern "C" void cm_default_options(cm_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->slack_pct = 25;
+    o->min_cap = 4;
+    o->block_threads = 512;
+    o->spin_limit_ns = 4000000000ll;
+}
+
+static void free_all(cm_graph* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaDeviceSynchronize();
+    DevGraph& g = h->g;
+    size_t nc = (size_t)h->ncap;
+    dfree(h, g.hs, nc * sizeof(int4));
+    dfree(h, g.off, nc * 8);
+    dfree(h, g.end, nc * 4);
+    dfree(h, g.cap, nc * 4);
+    dfree(h, g.deg, nc * 4);
+    dfree(h, g.chg, nc * 4);
+    dfree(h, g.taken, nc * 4);
+    dfree(h, g.claim0, nc * 8);
+    dfree(h, g.claim1, nc * 8);
+    dfree(h, g.need, nc * 4);
+    dfree(h, g.adj, (size_t)g.adj_cap * 4);
+    dfree(h, g.idx, h->idx_size * sizeof(Bucket));
+    size_t qn = h->qmask ? (size_t)(h->qmask + 1) : 0;
+    dfree(h, h->VQ, qn * 4);
+    dfree(h, h->EQ, qn * 4);
+    dfree(h, h->CQ, qn * 4);
+    dfree(h, h->OVL, qn * 4);
+    dfree(h, h->dbatch, (size_t)h->batch_cap * 8);
+    dfree(h, h->bset, h->bset_size * sizeof(BSet));
+    dfree(h, h->R0, (size_t)h->rcap * sizeof(REdge));
+    dfree(h, h->R1, (size_t)h->rcap * sizeof(REdge));
+    if (h->dbases) cudaFree(h->dbases);
+    if (h->dprefix) cudaFree(h->dprefix);
+    if (h->dpergraph) cudaFree(h->dpergraph);
+    if (h->ctl) cudaFree(h->ctl);
+    if (h->hctl) cudaFreeHost(h->hctl);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+static int peel_all(cm_graph* h);
+
+// Builds the store from a device edge list (global ids).
+static int build_store(cm_graph* h, const int32_t* dE, long long m, const int32_t* dcores) {
+    DevGraph& g = h->g;
+    uint32_t* ebkt = (uint32_t*)dalloc(h, (size_t)(m > 0 ? m : 1) * sizeof(uint32_t));
+    if (!ebkt) return set_err(h, CM_ERR_OOM, "out of device memory (create)");
+    int rc = CM_OK;
+    do {
+        if ((rc = reset_ingest_zone(h))) break;
+        h->launches += 3;
+        cudaError_t e = build_index(dE, m, g, ebkt, h->ctl, h->stream);
+        if (e == cudaSuccess) e = count_degrees(dE, ebkt, m, g, h->stream);
+        if (e == cudaSuccess) e = sum_caps(g, 0, g.n, h->ctl, h->stream);
+        if (e != cudaSuccess) { rc = fail_cuda(h, e, "build"); break; }
+        if ((rc = rd_ctl(h))) break;
+        if (h->hctl->error == E_INVALID) {
+            rc = set_err(h, CM_ERR_INVALID, "edge %lld has an id outside [0, %d)", h->hctl->bad_index, g.n);
+            break;
+        }
+        if (h->hctl->error) {
+            rc = set_err(h, CM_ERR_CUDA, "device error %d while building the index", h->hctl->error);
+            break;
+        }
+        long long total = (long long)h->hctl->reloc_need;
+        long long pool = total + total / 4 + 4096;
+        g.adj = (int32_t*)dalloc(h, (size_t)pool * sizeof(int32_t));
+        if (!g.adj) { rc = set_err(h, CM_ERR_OOM, "out of device memory for %lld adjacency slots", pool); break; }
+        g.adj_cap = pool;
+        if ((e = cudaMemsetAsync(&h->ctl->adj_top, 0, 8, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "memset"); break; }
+        h->launches += 2;
+        e = assign_offsets(g, 0, g.n, h->ctl, h->stream);
+        if (e == cudaSuccess) e = scatter_edges(dE, ebkt, m, g, h->stream);
+        if (e != cudaSuccess) { rc = fail_cuda(h, e, "scatter"); break; }
+        if (dcores) {
+            h->launches++;
+            if ((e = set_cores(dcores, g, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "set_cores"); break; }
+        } else {
+            if ((rc = peel_all(h))) break;
+        }
+        h->launches++;
+        if ((e = init_mcd(g, 0, g.n, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "init_mcd"); break; }
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "create"); break; }
+    } while (0);
+    cudaStreamSynchronize(h->stream);
+    dfree(h, ebkt, (size_t)(m > 0 ? m : 1) * sizeof(uint32_t));
+    return rc;
+}
+
+static int count_live_edges(cm_graph* h, long long* m) {
+    std::vector<int32_t> deg((size_t)h->n);
+    if (h->n) CK(h, cudaMemcpy(deg.data(), h->g.deg, (size_t)h->n * 4, cudaMemcpyDeviceToHost));
+    long long s = 0;
+    for (int32_t d : deg) s += d;
+    *m = s / 2;
+    return CM_OK;
+}
+
+// Creates a handle around n vertices and a DEVICE-or-host edge list.
+static int create_common(int32_t n, const int32_t* edges, long long m, const int32_t* cores, const cm_options* opt,
+                         void* stream, cm_graph** hout) {
+    cm_graph* h = new (std::nothrow) cm_graph();
+    if (!h) return set_err(nullptr, CM_ERR_OOM, "out of host memory");
+    *hout = h;
+    if (opt) h->opt = *opt; else cm_default_options(&h->opt);
+    if (h->opt.slack_pct < 0) h->opt.slack_pct = 0;
+    if (h->opt.min_cap < 4) h->opt.min_cap = 4;
+    if (h->opt.spin_limit_ns <= 0) h->opt.spin_limit_ns = 4000000000ll;
+    if (h->opt.block_threads <= 0 || h->opt.block_threads > 512 || h->opt.block_threads % 32)
+        h->opt.block_threads = 512;
+    h->stream = (cudaStream_t)stream;
+    CK(h, cudaGetDevice(&h->device));
+    CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    int coop = 0;
+    CK(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+    if (!coop) return set_err(h, CM_ERR_CUDA, "device does not support cooperative launches");
+    for (auto& e : h->ev) CK(h, cudaEventCreate(&e));
+    CK(h, cudaMalloc(&h->ctl, sizeof(Ctl)));
+    CK(h, cudaMemset(h->ctl, 0, sizeof(Ctl)));
+    CK(h, cudaMallocHost(&h->hctl, sizeof(Ctl)));
+    memset(h->hctl, 0, sizeof(Ctl));
+    h->g.n = n;
+    h->g.slack_pct = h->opt.slack_pct;
+    h->g.min_cap = h->opt.min_cap;
+    h->n = n;
+    int rc = grow_vertices(h, n > 0 ? n : 1);
+    if (rc) return rc;
+    if ((rc = alloc_index(h, pow2_at_least((unsigned long long)(2 * m + m / 2 + 1024))))) return rc;
+    const int32_t* dE = edges;
+    int32_t* tmp = nullptr;
+    if (m > 0 && !is_device_ptr(edges)) {
+        tmp = (int32_t*)dalloc(h, (size_t)m * 2 * sizeof(int32_t));
+        if (!tmp) return set_err(h, CM_ERR_OOM, "out of device memory for %lld input edges", m);
+        CK(h, cudaMemcpyAsync(tmp, edges, (size_t)m * 2 * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+        dE = tmp;
+    }
+    const int32_t* dC = cores;
+    int32_t* tmpc = nullptr;
+    if (cores && !is_device_ptr(cores)) {
+        tmpc = (int32_t*)dalloc(h, (size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        if (!tmpc) {
+            dfree(h, tmp, (size_t)m * 8);
+            return set_err(h, CM_ERR_OOM, "out of device memory for cores");
+        }
+        CK(h, cudaMemcpyAsync(tmpc, cores, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+        dC = tmpc;
+    }
+    rc = build_store(h, dE, m, dC);
+    cudaStreamSynchronize(h->stream);
+    dfree(h, tmp, (size_t)m * 8);
+    dfree(h, tmpc, (size_t)(n > 0 ? n : 1) * 4);
+    if (rc) return rc;
+    long long live = 0;
+    if ((rc = count_live_edges(h, &live))) return rc;
+    h->m = live;
+    h->idx_live = live;
+    h->bases = {0, n};
+    return CM_OK;
+}
+
+extern "C" int cm_create(cm_graph** out, int32_t n, const int32_t* edges, int64_t m, const int32_t* cores,
+                         const cm_options* opt, void* stream) {
+    if (!out) return set_err(nullptr, CM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || m < 0 || (m > 0 && !edges)) return set_err(nullptr, CM_ERR_INVALID, "bad sizes or NULL edges");
+    cm_graph* h = nullptr;
+    int rc = create_common(n, edges, m, cores, opt, stream, &h);
+    if (rc) {
+        if (h) {
+            g_create_err = h->err;
+            free_all(h);
+        }
+        return rc;
+    }
+    *out = h;
+    return CM_OK;
+}
+
+extern "C" void cm_destroy(cm_graph* h) { free_all(h); }
+
+// ------------------------------------------------------------------ peel
+static int peel_all(cm_graph* h) {
+    int rc = reset_launch_zone(h);
+    if (rc) return rc;
+    PeelParams p{};
+    p.g = h->g;
+    p.g.n = h->n;
+    p.ctl = h->ctl;
+    p.dcur = h->CQ;
+    p.L0 = h->VQ;
+    p.L1 = h->EQ;
+    p.F = h->OVL;
+    p.qmask = h->qmask;
+    p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
+    int blocks, threads;
+    persistent_geometry(h, 1, h->n, &blocks, &threads);
+    p.expect = (uint32_t)blocks;
+    LAUNCH(h, launch_peel(p, blocks, threads, h->stream));
+    if ((rc = rd_ctl(h))) return rc;
+    if (h->hctl->error) {
+        h->poisoned = true;
+        return set_err(h, CM_ERR_LIMIT, "peeling stopped with device error %d", h->hctl->error);
+    }
+    h->last.peel_levels = (int64_t)h->hctl->st[ST_LEVELS];
+    return CM_OK;
+}
+
+static int begin_call(cm_graph* h) {
+    if (!h) return CM_ERR_INVALID;
+    if (h->poisoned) return set_err(h, CM_ERR_STATE, "handle poisoned by an earlier failure: %s", h->err.c_str());
+    h->launches = 0;
+    memset(&h->last, 0, sizeof(h->last));
+    CK(h, cudaEventRecord(h->ev[0], h->stream));
+    return CM_OK;
+}
+
+static int end_call(cm_graph* h, int rc) {
+    if (rc == CM_OK) {
+        cudaEventRecord(h->ev[1], h->stream);
+        cudaEventSynchronize(h->ev[1]);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+        h->last.call_ms = ms;
+    }
+    h->last.launches = h->launches;
+    return rc;
+}
+
+extern "C" int cm_recompute_cores(cm_graph* h) {
+    int rc = begin_call(h);
+    if (rc) return rc;
+    CK(h, cudaEventRecord(h->ev[2], h->stream));
+    if ((rc = peel_all(h))) return end_call(h, rc);
+    DevGraph g = h->g;
+    g.n = h->n;
+    LAUNCH(h, init_mcd(g, 0, h->n, h->stream));
+    CK(h, cudaEventRecord(h->ev[3], h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+    h->last.maintain_ms = ms;
+    h->cores_stale = false;
+    return end_call(h, CM_OK);
+}
+
+// ------------------------------------------------------------------ updates
+// mode 0: maintain cores; mode 1: structure only (cores become stale).
+// per_graph (host, nullable): per-graph kept counts of a multi-graph batch.
+static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, int64_t* n_applied, int mode,
+                         int64_t* per_graph) {
+    DevGraph& g = h->g;
+    g.n = h->n;
+    int rc;
+    if (op == CM_OP_INSERT && (rc = ensure_index(h, k))) return rc;
+    CK(h, cudaMemsetAsync(h->bset, 0xFF, h->bset_size * sizeof(BSet), h->stream));
+    if ((rc = reset_ingest_zone(h))) return rc;
+    LAUNCH(h, ingest_a(dE, k, g, h->bset, h->bset_size - 1, h->ctl, h->stream));
+    LAUNCH(h, ingest_b(dE, k, op, g, h->bset, h->bset_size - 1, h->R0, h->OVL, h->ctl, h->stream));
+    if ((rc = rd_ctl(h))) return rc;
+    Ctl& c = *h->hctl;
+    if (c.error == E_INVALID)
+        return set_err(h, CM_ERR_INVALID, "edge %lld of the batch names a vertex out of range or deleted", c.bad_index);
+    if (c.error) {
+        h->poisoned = true;
+        return set_err(h, CM_ERR_CUDA, "device error %d during ingest", c.error);
+    }
+    const long long nrem0 = (long long)c.nrem;
+    if (per_graph && h->dpergraph) {
+        CK(h, cudaMemsetAsync(h->dpergraph, 0, (size_t)h->ngraphs * 8, h->stream));
+        LAUNCH(h, count_multi(h->R0, nrem0, h->dbases, h->ngraphs, h->dpergraph, h->stream));
+        CK(h, cudaMemcpyAsync(per_graph, h->dpergraph, (size_t)h->ngraphs * 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    if (op == CM_OP_INSERT) {
+        h->idx_live += nrem0;
+        const long long novl = (long long)c.noverflow;
+        if (novl > 0) {
+            LAUNCH(h, reloc_size(h->OVL, novl, g, h->ctl, h->stream));
+            if ((rc = rd_ctl(h))) return rc;
+            if ((rc = grow_pool(h, (long long)h->hctl->reloc_need))) {
+                h->poisoned = true;
+                return rc;
+            }
+            LAUNCH(h, relocate(h->OVL, novl, h->g, h->ctl, h->stream));
+        }
+        LAUNCH(h, clear_need(h->R0, nrem0, h->g, h->stream));
+    }
+    if (nrem0 > 0 && mode == 1) {
+        LAUNCH(h, apply_structure(h->R0, nrem0, op, h->g, h->ctl, h->stream));
+        if ((rc = rd_ctl(h))) return rc;
+        if (c.error) {
+            h->poisoned = true;
+            return set_err(h, CM_ERR_LIMIT, "structure update failed with device error %d", c.error);
+        }
+    } else if (nrem0 > 0) {
+        if (h->epoch > 0xF0000000u) {   // stamps about to wrap: clear them
+            CK(h, cudaMemsetAsync(g.chg, 0, (size_t)h->n * 4, h->stream));
+            CK(h, cudaMemsetAsync(g.taken, 0, (size_t)h->n * 4, h->stream));
+            CK(h, cudaMemset2DAsync((char*)g.hs + 8, sizeof(int4), 0, 8, (size_t)h->n, h->stream));
+            h->epoch = 1;
+        }
+        if ((rc = reset_launch_zone(h))) return rc;
+        MaintainParams p{};
+        p.g = h->g;
+        p.ctl = h->ctl;
+        p.R0 = h->R0;
+        p.R1 = h->R1;
+        p.nrem0 = (unsigned long long)nrem0;
+        p.VQ = h->VQ;
+        p.EQ = h->EQ;
+        p.CQ = h->CQ;
+        p.qmask = h->qmask;
+        p.epoch0 = h->epoch;
+        p.op = op;
+        p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
+        p.max_iters = nrem0 + 1;
+        int blocks, threads;
+        persistent_geometry(h, 0, nrem0, &blocks, &threads);
+        p.expect = (uint32_t)blocks;
+        if (h->opt.debug_flags & CM_DEBUG_BARRIER_NEVER_RELEASES) {
+            p.expect = (uint32_t)blocks + 1;   // test hook: no barrier can complete
+            h->opt.debug_flags &= ~CM_DEBUG_BARRIER_NEVER_RELEASES;
+        }
+        CK(h, cudaEventRecord(h->ev[2], h->stream));
+        LAUNCH(h, launch_maintain(p, blocks, threads, h->stream));
+        CK(h, cudaEventRecord(h->ev[3], h->stream));
+        if ((rc = rd_ctl(h))) return rc;
+        if (c.error) {
+            h->poisoned = true;
+            const char* why = c.error == E_BARRIER_TIMEOUT ? "a grid barrier wait ran out"
+                              : c.error == E_ITER_LIMIT   ? "an iteration or retry limit ran out"
+                              : c.error == E_CAPACITY     ? "an adjacency list overflowed"
+                                                          : "device error";
+            return set_err(h, CM_ERR_LIMIT, "maintenance stopped: %s (code %d)", why, c.error);
+        }
+        h->epoch = (uint32_t)c.wc;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+        cm_stats& s = h->last;
+        s.maintain_ms += ms;
+        s.iterations += (int64_t)c.st[ST_ITERS];
+        s.select_rounds += (int64_t)c.st[ST_ROUNDS];
+        s.selected += (int64_t)c.st[ST_SELECTED];
+        s.remaining_sum += (int64_t)c.st[ST_REMSUM];
+        s.visited += (int64_t)c.st[ST_VISITED];
+        s.visited_slots += (int64_t)c.st[ST_VISSLOTS];
+        s.evicted += (int64_t)c.st[ST_EVICTED];
+        s.evicted_slots += (int64_t)c.st[ST_EVSLOTS];
+        s.changed += (int64_t)c.st[ST_CHANGED];
+        s.changed_slots += (int64_t)c.st[ST_CHSLOTS];
+        s.waves += (int64_t)c.st[ST_WAVES];
+        // Algorithmic bytes of the maintenance launch: per iteration 16 B per
+        // remaining edge (pair + both cores) and 16 B per selected edge
+        // (claims, CSR writes); 16 B per visited vertex (its row) plus 12 B
+        // per slot (neighbour id, core, SD); 12 B per slot of an evicted
+        // vertex (id, core, support update); 8 B per changed vertex plus 8 B
+        // per slot (id, core) for the SD fix-up.
+        s.alg_bytes += 16 * (int64_t)c.st[ST_REMSUM] + 16 * (int64_t)c.st[ST_SELECTED] +
+                       16 * (int64_t)c.st[ST_VISITED] + 12 * (int64_t)c.st[ST_VISSLOTS] +
+                       12 * (int64_t)c.st[ST_EVSLOTS] + 8 * (int64_t)c.st[ST_CHANGED] +
+                       8 * (int64_t)c.st[ST_CHSLOTS];
+    }
+    if (op == CM_OP_DELETE) {
+        h->idx_live -= nrem0;
+        h->idx_tomb += nrem0;
+        h->m -= nrem0;
+    } else {
+        h->m += nrem0;
+    }
+    h->last.applied += nrem0;
+    if (n_applied) *n_applied = nrem0;
+    return CM_OK;
+}
+
+static int stage_edges(cm_graph* h, const int32_t* edges, long long k, const int32_t** dE) {
+    int rc = ensure_batch(h, k);
+    if (rc) return rc;
+    if (is_device_ptr(edges)) {
+        *dE = edges;
+    } else {
+        CK(h, cudaMemcpyAsync(h->dbatch, edges, (size_t)k * 2 * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+        *dE = h->dbatch;
+    }
+    return CM_OK;
+}
+
+static int update_edges(cm_graph* h, int op, const int32_t* edges, long long k, int64_t* n_applied, int mode) {
+    int rc = begin_call(h);
+    if (rc) return rc;
+    if (k < 0 || (k > 0 && !edges)) return end_call(h, set_err(h, CM_ERR_INVALID, "bad batch size or NULL edges"));
+    if (mode == 0 && h->cores_stale)
+        return end_call(h, set_err(h, CM_ERR_STATE, "cores are stale: call cm_recompute_cores"));
+    if (k == 0) {
+        if (n_applied) *n_applied = 0;
+        return end_call(h, CM_OK);
+    }
+    const int32_t* dE = nullptr;
+    if ((rc = stage_edges(h, edges, k, &dE))) return end_call(h, rc);
+    return end_call(h, update_device(h, op, dE, k, n_applied, mode, nullptr));
+}
+
+extern "C" int cm_insert_edges(cm_graph* h, const int32_t* edges, int64_t k, int64_t* n_applied) {
+    return update_edges(h, CM_OP_INSERT, edges, k, n_applied, 0);
+}
+extern "C" int cm_delete_edges(cm_graph* h, const int32_t* edges, int64_t k, int64_t* n_applied) {
+    return update_edges(h, CM_OP_DELETE, edges, k, n_applied, 0);
+}
+extern "C" int cm_apply_edges(cm_graph* h, int32_t op, const int32_t* edges, int64_t k, int64_t* n_applied) {
+    if (op != CM_OP_INSERT && op != CM_OP_DELETE) return h ? set_err(h, CM_ERR_INVALID, "bad op") : CM_ERR_INVALID;
+    int rc = update_edges(h, op, edges, k, n_applied, 1);
+    if (rc == CM_OK) h->cores_stale = true;
+    return rc;
+}
+
+// ------------------------------------------------------------------ vertex operations
+extern "C" int cm_insert_vertices(cm_graph* h, int32_t count, const int64_t* nbr_off, const int32_t* nbrs,
+                                  int32_t* first_id, int64_t* n_applied) {
+    int rc = begin_call(h);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && !nbr_off))
+        return end_call(h, set_err(h, CM_ERR_INVALID, "bad vertex count or NULL offsets"));
+    if (h->cores_stale) return end_call(h, set_err(h, CM_ERR_STATE, "cores are stale"));
+    if ((long long)h->n + count > INT32_MAX) return end_call(h, set_err(h, CM_ERR_CAPACITY, "vertex ids would exceed int32"));
+    if (count == 0) {
+        if (first_id) *first_id = h->n;
+        if (n_applied) *n_applied = 0;
+        return end_call(h, CM_OK);
+    }
+    std::vector<int64_t> hoff((size_t)count + 1);
+    if (is_device_ptr(nbr_off)) CK(h, cudaMemcpy(hoff.data(), nbr_off, hoff.size() * 8, cudaMemcpyDeviceToHost));
+    else memcpy(hoff.data(), nbr_off, hoff.size() * 8);
+    if (hoff[0] != 0) return end_call(h, set_err(h, CM_ERR_INVALID, "nbr_off[0] must be 0"));
+    long long slots = 0;
+    for (int32_t i = 0; i < count; i++) {
+        long long d = hoff[i + 1] - hoff[i];
+        if (d < 0) return end_call(h, set_err(h, CM_ERR_INVALID, "nbr_off must be non-decreasing"));
+        long long c = (d * (100 + h->opt.slack_pct) + 99) / 100;
+        if (c < h->opt.min_cap) c = h->opt.min_cap;
+        slots += (c + 3) & ~3ll;
+    }
+    const long long tot = hoff[count];
+    if (tot > 0 && !nbrs) return end_call(h, set_err(h, CM_ERR_INVALID, "NULL neighbour list"));
+    // staging in the batch buffer: [edges 2*tot int32][offsets count+1 int64][neighbours tot int32]
+    long long ints = 2 * tot + 2 * ((long long)count + 1) + tot + 8;
+    if ((rc = ensure_batch(h, (ints + 1) / 2 > tot ? (ints + 1) / 2 : tot))) return end_call(h, rc);
+    int64_t* doff = (int64_t*)(h->dbatch + 2 * tot);
+    int32_t* dnb = (int32_t*)(doff + count + 1);
+    CK(h, cudaMemcpyAsync(doff, hoff.data(), hoff.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    const int32_t* nbsrc = nbrs;
+    if (tot > 0 && !is_device_ptr(nbrs)) {
+        CK(h, cudaMemcpyAsync(dnb, nbrs, (size_t)tot * 4, cudaMemcpyHostToDevice, h->stream));
+        nbsrc = dnb;
+    }
+    if ((rc = reset_ingest_zone(h))) return end_call(h, rc);
+    DevGraph g = h->g;
+    g.n = h->n;
+    LAUNCH(h, validate_vertices(doff, nbsrc, count, h->n, g, h->ctl, h->stream));
+    if ((rc = rd_ctl(h))) return end_call(h, rc);
+    if (h->hctl->error)
+        return end_call(h, set_err(h, CM_ERR_INVALID, "neighbour %lld is out of range, deleted or the vertex itself",
+                                   h->hctl->bad_index));
+    if ((rc = grow_vertices(h, h->n + count))) return end_call(h, rc);
+    if ((rc = grow_pool(h, slots))) return end_call(h, rc);
+    const int32_t base = h->n;
+    LAUNCH(h, init_vertices(doff, count, base, h->g, h->ctl, h->stream));
+    LAUNCH(h, expand_vertex_edges(doff, nbsrc, count, base, h->dbatch, h->stream));
+    h->n += count;
+    h->g.n = h->n;
+    if (first_id) *first_id = base;
+    int64_t applied = 0;
+    rc = tot > 0 ? update_device(h, CM_OP_INSERT, h->dbatch, tot, &applied, 0, nullptr) : CM_OK;
+    if (rc == CM_OK) {
+        if (n_applied) *n_applied = applied;
+    } else {
+        h->poisoned = true;   // the vertices exist but their edges failed
+    }
+    return end_call(h, rc);
+}
+
+extern "C" int cm_insert_vertex(cm_graph* h, const int32_t* nbrs, int32_t d, int32_t* new_id) {
+    if (!h) return CM_ERR_INVALID;
+    if (d < 0) return set_err(h, CM_ERR_INVALID, "negative degree");
+    int64_t off[2] = {0, d};
+    return cm_insert_vertices(h, 1, off, nbrs, new_id, nullptr);
+}
+
+extern "C" int cm_delete_vertices(cm_graph* h, int32_t count, const int32_t* ids, int64_t* n_applied) {
+    int rc = begin_call(h);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && !ids)) return end_call(h, set_err(h, CM_ERR_INVALID, "bad count or NULL ids"));
+    if (h->cores_stale) return end_call(h, set_err(h, CM_ERR_STATE, "cores are stale"));
+    if (count == 0) {
+        if (n_applied) *n_applied = 0;
+        return end_call(h, CM_OK);
+    }
+    int32_t* dids = (int32_t*)dalloc(h, (size_t)count * 4);
+    if (!dids) return end_call(h, set_err(h, CM_ERR_OOM, "out of device memory"));
+    do {
+        cudaError_t e = cudaMemcpyAsync(dids, ids, (size_t)count * 4,
+                                        is_device_ptr(ids) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) { rc = fail_cuda(h, e, "copy ids"); break; }
+        if ((rc = reset_ingest_zone(h))) break;
+        DevGraph g = h->g;
+        g.n = h->n;
+        h->launches++;
+        if ((e = validate_ids(dids, count, g, h->ctl, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "validate_ids"); break; }
+        if ((rc = rd_ctl(h))) break;
+        if (h->hctl->error) {
+            rc = set_err(h, CM_ERR_INVALID, "vertex at position %lld is out of range or already deleted", h->hctl->bad_index);
+            break;
+        }
+        long long bound = (long long)h->hctl->reloc_need;
+        if ((rc = ensure_batch(h, bound + 8))) break;
+        if ((rc = reset_ingest_zone(h))) break;
+        h->launches++;
+        if ((e = gather_incident(dids, count, g, h->dbatch, bound, h->ctl, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "gather"); break; }
+        if ((rc = rd_ctl(h))) break;
+        long long k = (long long)h->hctl->gather_n;
+        int64_t applied = 0;
+        if (k > 0 && (rc = update_device(h, CM_OP_DELETE, h->dbatch, k, &applied, 0, nullptr))) break;
+        h->launches++;
+        if ((e = mark_dead(dids, count, h->g, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "mark_dead"); break; }
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "sync"); break; }
+        if (n_applied) *n_applied = applied;
+    } while (0);
+    cudaStreamSynchronize(h->stream);
+    dfree(h, dids, (size_t)count * 4);
+    return end_call(h, rc);
+}
+
+extern "C" int cm_delete_vertex(cm_graph* h, int32_t v) {
+    int32_t ids[1] = {v};
+    return cm_delete_vertices(h, 1, ids, nullptr);
+}
+
+// ------------------------------------------------------------------ queries
+extern "C" int cm_get_cores(const cm_graph* hc, int32_t* out, int32_t* n_total) {
+    cm_graph* h = const_cast<cm_graph*>(hc);
+    if (!h) return CM_ERR_INVALID;
+    if (h->poisoned) return set_err(h, CM_ERR_STATE, "handle poisoned: %s", h->err.c_str());
+    if (n_total) *n_total = h->n;
+    if (!out) return CM_OK;
+    if (h->cores_stale) return set_err(h, CM_ERR_STATE, "cores are stale: call cm_recompute_cores");
+    DevGraph g = h->g;
+    g.n = h->n;
+    if (is_device_ptr(out)) {
+        LAUNCH(h, export_cores(g, out, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return CM_OK;
+    }
+    LAUNCH(h, export_cores(g, h->CQ, h->stream));   // CQ holds >= n entries
+    CK(h, cudaMemcpyAsync(out, h->CQ, (size_t)h->n * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return CM_OK;
+}
+
+extern "C" int cm_get_edges(const cm_graph* hc, int32_t* out, int64_t cap, int64_t* m) {
+    cm_graph* h = const_cast<cm_graph*>(hc);
+    if (!h) return CM_ERR_INVALID;
+    if (h->poisoned) return set_err(h, CM_ERR_STATE, "handle poisoned: %s", h->err.c_str());
+    if (m) *m = h->m;
+    if (!out) return CM_OK;
+    if (cap < h->m) return set_err(h, CM_ERR_CAPACITY, "capacity %lld < %lld edges", (long long)cap, (long long)h->m);
+    int rc = reset_ingest_zone(h);
+    if (rc) return rc;
+    DevGraph g = h->g;
+    g.n = h->n;
+    bool dev = is_device_ptr(out);
+    int32_t* dst = out;
+    size_t bytes = (size_t)(h->m > 0 ? h->m : 1) * 8;
+    if (!dev) {
+        dst = (int32_t*)dalloc(h, bytes);
+        if (!dst) return set_err(h, CM_ERR_OOM, "out of device memory");
+    }
+    LAUNCH(h, export_edges(g, dst, h->ctl, h->stream));
+    if (!dev) CK(h, cudaMemcpyAsync(out, dst, (size_t)h->m * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!dev) dfree(h, dst, bytes);
+    return CM_OK;
+}
+
+extern "C" int32_t cm_num_vertices(const cm_graph* h) { return h ? h->n : -1; }
+extern "C" int64_t cm_num_edges(const cm_graph* h) { return h ? h->m : -1; }
+
+extern "C" int cm_get_stats(const cm_graph* h, cm_stats* out) {
+    if (!h || !out) return CM_ERR_INVALID;
+    *out = h->last;
+    return CM_OK;
+}
+
+extern "C" int cm_set_stream(cm_graph* h, void* stream) {
+    if (!h) return CM_ERR_INVALID;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->stream = (cudaStream_t)stream;
+    return CM_OK;
+}
+
+extern "C" const char* cm_last_error(const cm_graph* h) {
+    if (!h) return g_create_err.c_str();
+    return h->err.c_str();
+}
+
+// ------------------------------------------------------------------ multi-graph
+extern "C" int cm_create_multi(cm_graph** out, int32_t ngraphs, const int32_t* ns, const int64_t* ms,
+                               const int32_t* edges, const int32_t* cores, const cm_options* opt, void* stream) {
+    if (!out || ngraphs <= 0 || !ns || !ms) return set_err(nullptr, CM_ERR_INVALID, "bad multi-graph arguments");
+    *out = nullptr;
+    std::vector<int32_t> bases((size_t)ngraphs + 1, 0);
+    std::vector<long long> eprefix((size_t)ngraphs + 1, 0);
+    long long nt = 0;
+    for (int32_t i = 0; i < ngraphs; i++) {
+        if (ns[i] < 0 || ms[i] < 0) return set_err(nullptr, CM_ERR_INVALID, "negative size for graph %d", i);
+        bases[i] = (int32_t)nt;
+        nt += ns[i];
+        eprefix[i + 1] = eprefix[i] + ms[i];
+        if (nt > INT32_MAX) return set_err(nullptr, CM_ERR_CAPACITY, "total vertex count exceeds int32");
+    }
+    bases[ngraphs] = (int32_t)nt;
+    const long long mt = eprefix[ngraphs];
+    if (mt > 0 && !edges) return set_err(nullptr, CM_ERR_INVALID, "NULL edges");
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t* dE = nullptr;
+    int32_t* dB = nullptr;
+    long long* dP = nullptr;
+    unsigned long long* dG = nullptr;
+    if (cudaMalloc(&dE, (size_t)(mt > 0 ? mt : 1) * 8) != cudaSuccess || cudaMalloc(&dB, bases.size() * 4) != cudaSuccess ||
+        cudaMalloc(&dP, eprefix.size() * 8) != cudaSuccess || cudaMalloc(&dG, bases.size() * 8) != cudaSuccess) {
+        cudaGetLastError();
+        if (dE) cudaFree(dE);
+        if (dB) cudaFree(dB);
+        if (dP) cudaFree(dP);
+        if (dG) cudaFree(dG);
+        return set_err(nullptr, CM_ERR_OOM, "out of device memory");
+    }
+    bool ok = true;
+    if (mt > 0)
+        ok = ok && cudaMemcpyAsync(dE, edges, (size_t)mt * 8,
+                                   is_device_ptr(edges) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(dB, bases.data(), bases.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(dP, eprefix.data(), eprefix.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && localize_multi(dE, mt, dP, dB, ngraphs, s) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    int rc = CM_OK;
+    cm_graph* h = nullptr;
+    if (!ok) {
+        rc = set_err(nullptr, CM_ERR_CUDA, "CUDA error while staging a multi-graph");
+    } else {
+        rc = create_common((int32_t)nt, dE, mt, cores, opt, stream, &h);
+        if (rc) {
+            if (h) {
+                g_create_err = h->err;
+                free_all(h);
+                h = nullptr;
+            }
+        }
+    }
+    cudaFree(dE);
+    if (!h) {
+        cudaFree(dB);
+        cudaFree(dP);
+        cudaFree(dG);
+        return rc;
+    }
+    h->ngraphs = ngraphs;
+    h->bases = bases;
+    h->dbases = dB;
+    h->dprefix = dP;
+    h->dpergraph = dG;
+    *out = h;
+    return CM_OK;
+}
+
+extern "C" int cm_multi_bases(const cm_graph* h, int32_t* bases, int32_t* ngraphs) {
+    if (!h) return CM_ERR_INVALID;
+    if (ngraphs) *ngraphs = h->ngraphs;
+    if (bases)
+        for (int32_t i = 0; i < h->ngraphs; i++) bases[i] = h->bases[(size_t)i];
+    return CM_OK;
+}
+
+extern "C" int cm_update_multi(cm_graph* h, int32_t op, const int64_t* counts, const int32_t* edges,
+                               int64_t* n_applied) {
+    int rc = begin_call(h);
+    if (rc) return rc;
+    if ((op != CM_OP_INSERT && op != CM_OP_DELETE) || !counts)
+        return end_call(h, set_err(h, CM_ERR_INVALID, "bad arguments"));
+    if (h->cores_stale) return end_call(h, set_err(h, CM_ERR_STATE, "cores are stale"));
+    if (!h->dprefix) return end_call(h, set_err(h, CM_ERR_STATE, "not a multi-graph handle"));
+    const int32_t ng = h->ngraphs;
+    std::vector<long long> pre((size_t)ng + 1, 0);
+    for (int32_t i = 0; i < ng; i++) {
+        if (counts[i] < 0) return end_call(h, set_err(h, CM_ERR_INVALID, "negative count for graph %d", i));
+        pre[i + 1] = pre[i] + counts[i];
+    }
+    const long long k = pre[ng];
+    if (k == 0) {
+        if (n_applied)
+            for (int32_t i = 0; i < ng; i++) n_applied[i] = 0;
+        return end_call(h, CM_OK);
+    }
+    if (!edges) return end_call(h, set_err(h, CM_ERR_INVALID, "NULL edges"));
+    if ((rc = ensure_batch(h, k))) return end_call(h, rc);
+    CK(h, cudaMemcpyAsync(h->dbatch, edges, (size_t)k * 8,
+                          is_device_ptr(edges) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->dprefix, pre.data(), pre.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    LAUNCH(h, localize_multi(h->dbatch, k, h->dprefix, h->dbases, ng, h->stream));
+    int64_t applied = 0;
+    std::vector<int64_t> per((size_t)ng, 0);
+    rc = update_device(h, op, h->dbatch, k, &applied, 0, per.data());
+    if (rc) return end_call(h, rc);
+    if (n_applied)
+        for (int32_t i = 0; i < ng; i++) n_applied[i] = per[(size_t)i];
+    return end_call(h, CM_OK);
+}

@@ -1,0 +1,87 @@
+// cm_launch.h -- host-side declarations of the kernel launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cm_common.cuh"
+
+namespace cm {
+
+// Batch-dedupe hash set entry: key -> smallest input position.
+struct __align__(16) BSet {
+    unsigned long long key;
+    uint32_t pos;
+    uint32_t pad;
+};
+
+struct MaintainParams {
+    DevGraph g;
+    Ctl* ctl;
+    REdge* R0;
+    REdge* R1;
+    unsigned long long nrem0;
+    int32_t* VQ;
+    int32_t* EQ;
+    int32_t* CQ;
+    unsigned long long qmask;
+    uint32_t epoch0;
+    int32_t op;               // 0 insert, 1 delete
+    uint32_t expect;          // blocks a grid barrier waits for
+    uint32_t pad;
+    unsigned long long limit_ns;
+    long long max_iters;
+};
+
+struct PeelParams {
+    DevGraph g;
+    Ctl* ctl;
+    int32_t* dcur;    // working degree [n]
+    int32_t* L0;      // remaining-vertex lists [n]
+    int32_t* L1;
+    int32_t* F;       // frontier ring [qmask+1]
+    unsigned long long qmask;
+    uint32_t expect;
+    uint32_t pad;
+    unsigned long long limit_ns;
+};
+
+// ---- maintenance (cm_maintain.cu)
+cudaError_t ingest_a(const int32_t* E, long long k, DevGraph g, BSet* bs, unsigned long long bmask, Ctl* c,
+                     cudaStream_t s);
+cudaError_t ingest_b(const int32_t* E, long long k, int op, DevGraph g, const BSet* bs, unsigned long long bmask,
+                     REdge* R0, int32_t* ovl, Ctl* c, cudaStream_t s);
+cudaError_t reloc_size(const int32_t* ovl, long long novl, DevGraph g, Ctl* c, cudaStream_t s);
+cudaError_t relocate(const int32_t* ovl, long long novl, DevGraph g, Ctl* c, cudaStream_t s);
+cudaError_t clear_need(const REdge* R, long long n, DevGraph g, cudaStream_t s);
+cudaError_t apply_structure(const REdge* R, long long n, int op, DevGraph g, Ctl* c, cudaStream_t s);
+cudaError_t launch_maintain(const MaintainParams& p, int blocks, int threads, cudaStream_t s);
+int maintain_blocks_per_sm(int threads);
+
+// ---- store / peel (cm_store.cu)
+cudaError_t build_index(const int32_t* E, long long m, DevGraph g, uint32_t* ebkt, Ctl* c, cudaStream_t s);
+cudaError_t count_degrees(const int32_t* E, const uint32_t* ebkt, long long m, DevGraph g, cudaStream_t s);
+cudaError_t assign_offsets(DevGraph g, int32_t v0, int32_t v1, Ctl* c, cudaStream_t s);
+cudaError_t scatter_edges(const int32_t* E, const uint32_t* ebkt, long long m, DevGraph g, cudaStream_t s);
+cudaError_t set_cores(const int32_t* cores, DevGraph g, cudaStream_t s);
+cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, cudaStream_t s);
+cudaError_t launch_peel(const PeelParams& p, int blocks, int threads, cudaStream_t s);
+int peel_blocks_per_sm(int threads);
+cudaError_t rehash(const Bucket* old_idx, unsigned long long old_size, DevGraph g, Ctl* c, cudaStream_t s);
+cudaError_t validate_vertices(const int64_t* nbr_off, const int32_t* nbrs, int32_t count, int32_t base, DevGraph g,
+                              Ctl* c, cudaStream_t s);
+cudaError_t init_vertices(const int64_t* nbr_off, int32_t count, int32_t base, DevGraph g, Ctl* c, cudaStream_t s);
+cudaError_t expand_vertex_edges(const int64_t* nbr_off, const int32_t* nbrs, int32_t count, int32_t base, int32_t* E,
+                                cudaStream_t s);
+cudaError_t validate_ids(const int32_t* ids, int32_t count, DevGraph g, Ctl* c, cudaStream_t s);
+cudaError_t gather_incident(const int32_t* ids, int32_t count, DevGraph g, int32_t* E, long long cap, Ctl* c,
+                            cudaStream_t s);
+cudaError_t mark_dead(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s);
+cudaError_t export_cores(DevGraph g, int32_t* out, cudaStream_t s);
+cudaError_t export_edges(DevGraph g, int32_t* out, Ctl* c, cudaStream_t s);
+cudaError_t localize_multi(int32_t* E, long long k, const long long* prefix, const int32_t* bases, int32_t ng,
+                           cudaStream_t s);
+cudaError_t sum_caps(DevGraph g, int32_t v0, int32_t v1, Ctl* c, cudaStream_t s);
+cudaError_t count_multi(const REdge* R, long long n, const int32_t* bases, int32_t ng, unsigned long long* per_graph,
+                        cudaStream_t s);
+
+}  // namespace cm

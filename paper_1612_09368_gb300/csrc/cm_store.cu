@@ -1,0 +1,530 @@
+// cm_store.cu -- device graph store: construction, full decomposition by
+// bucket peeling, superior degrees, vertex insertion/deletion helpers and
+// export.
+#include "cm_common.cuh"
+#include "cm_launch.h"
+
+namespace cm {
+
+constexpr uint32_t BKT_DROP = 0xFFFFFFFFu;
+constexpr int UNPEELED = -2;
+
+static inline unsigned grid_for(long long n, int t, long long cap = 1 << 20) {
+    long long b = (n + t - 1) / t;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+// ------------------------------------------------------------------ construction
+// Validate ids, drop self-loops and repeats (first index insertion wins),
+// record each kept edge's bucket.
+__global__ void build_index_kernel(const int32_t* __restrict__ E, long long m, DevGraph g, uint32_t* ebkt, Ctl* c) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int32_t u = E[2 * i], v = E[2 * i + 1];
+    ebkt[i] = BKT_DROP;
+    if (u < 0 || v < 0 || u >= g.n || v >= g.n) {
+        atomicMin(&c->bad_index, i);
+        atomicCAS(&c->error, 0, E_INVALID);
+        return;
+    }
+    if (u == v) return;
+    bool existed = false;
+    long long b = idx_insert(g.idx, g.idx_mask, ekey(u, v), &existed);
+    if (b < 0) { atomicCAS(&c->error, 0, E_INDEX_FULL); return; }
+    if (existed) return;
+    g.idx[b].slo = -2;
+    g.idx[b].shi = -2;
+    ebkt[i] = (uint32_t)b;
+}
+
+__global__ void count_degrees_kernel(const int32_t* __restrict__ E, const uint32_t* __restrict__ ebkt, long long m,
+                                     DevGraph g) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || ebkt[i] == BKT_DROP) return;
+    atomicAdd(&g.deg[E[2 * i]], 1);
+    atomicAdd(&g.deg[E[2 * i + 1]], 1);
+}
+
+// Sum of capacities (into c->reloc_need) when sum_only, else assign each
+// vertex of [v0, v1) a slot range by a warp-level scan and one pool
+// allocation per warp.
+__global__ void offsets_kernel(DevGraph g, int32_t v0, int32_t v1, Ctl* c, int sum_only) {
+    long long base = (long long)v0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll);
+    long long stride = (long long)gridDim.x * blockDim.x;
+    int lane = lane_id();
+    for (; base < v1; base += stride) {
+        long long v = base + lane;
+        int cp = 0;
+        if (v < v1) cp = cap_for(g.deg[v], g.slack_pct, g.min_cap);
+        int incl = cp;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long wb = 0;
+        if (lane == 31) wb = atomicAdd(sum_only ? &c->reloc_need : &c->adj_top, (unsigned long long)tot);
+        wb = __shfl_sync(0xffffffffu, wb, 31);
+        if (!sum_only && v < v1) {
+            g.off[v] = (int64_t)(wb + incl - cp);
+            g.cap[v] = cp;
+            g.end[v] = 0;
+        }
+    }
+}
+
+__global__ void scatter_kernel(const int32_t* __restrict__ E, const uint32_t* __restrict__ ebkt, long long m,
+                               DevGraph g) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t b = ebkt[i];
+    if (b == BKT_DROP) return;
+    int32_t lo = min(E[2 * i], E[2 * i + 1]), hi = max(E[2 * i], E[2 * i + 1]);
+    int pu = atomicAdd(&g.end[lo], 1), pv = atomicAdd(&g.end[hi], 1);
+    g.adj[g.off[lo] + pu] = hi;
+    g.adj[g.off[hi] + pv] = lo;
+    g.idx[b].slo = pu;
+    g.idx[b].shi = pv;
+}
+
+__global__ void set_cores_kernel(const int32_t* __restrict__ cores, DevGraph g) {
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n) return;
+    g.hs[v].x = cores[v];
+}
+
+// SD(v), Definition 7: neighbours with core >= core(v).  Warp per vertex.
+__global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1) {
+    long long w = v0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int lane = lane_id();
+    for (; w < v1; w += nw) {
+        int k = g.hs[w].x;
+        if (k < 0) continue;
+        long long o = g.off[w];
+        int len = g.end[w], sd = 0;
+        for (int t = lane; t < len; t += 32) {
+            int x = g.adj[o + t];
+            if (x >= 0 && g.hs[x].x >= k) sd++;
+        }
+        sd = warp_sum(sd);
+        if (lane == 0) g.hs[w].y = sd;
+    }
+}
+
+cudaError_t build_index(const int32_t* E, long long m, DevGraph g, uint32_t* ebkt, Ctl* c, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    build_index_kernel<<<grid_for(m, 256, 1ll << 31), 256, 0, s>>>(E, m, g, ebkt, c);
+    return cudaGetLastError();
+}
+cudaError_t count_degrees(const int32_t* E, const uint32_t* ebkt, long long m, DevGraph g, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    count_degrees_kernel<<<grid_for(m, 256, 1ll << 31), 256, 0, s>>>(E, ebkt, m, g);
+    return cudaGetLastError();
+}
+cudaError_t assign_offsets(DevGraph g, int32_t v0, int32_t v1, Ctl* c, cudaStream_t s) {
+    if (v1 <= v0) return cudaSuccess;
+    offsets_kernel<<<grid_for(v1 - v0, 256, 65536), 256, 0, s>>>(g, v0, v1, c, 0);
+    return cudaGetLastError();
+}
+cudaError_t scatter_edges(const int32_t* E, const uint32_t* ebkt, long long m, DevGraph g, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    scatter_kernel<<<grid_for(m, 256, 1ll << 31), 256, 0, s>>>(E, ebkt, m, g);
+    return cudaGetLastError();
+}
+cudaError_t set_cores(const int32_t* cores, DevGraph g, cudaStream_t s) {
+    if (g.n <= 0) return cudaSuccess;
+    set_cores_kernel<<<grid_for(g.n, 256, 1ll << 31), 256, 0, s>>>(cores, g);
+    return cudaGetLastError();
+}
+cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, cudaStream_t s) {
+    if (v1 <= v0) return cudaSuccess;
+    init_mcd_kernel<<<grid_for((long long)(v1 - v0) * 32, 256, 65536), 256, 0, s>>>(g, v0, v1);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ peeling
+// Level-synchronous bucket peeling (the static O(m) decomposition the paper
+// cites, run level by level): at level k every remaining vertex whose
+// degree is <= k gets core k and leaves; each departure takes one degree
+// from every remaining neighbour, and neighbours that reach k leave at the
+// same level.  Empty levels are skipped to the smallest remaining degree.
+__global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
+    Ctl* C = P.ctl;
+    const DevGraph g = P.g;
+    const int lane = lane_id();
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
+    bool ok;
+    // live vertices start unpeeled with their live degree
+    for (long long base = gwarp * 32; base < g.n; base += nwarps * 32) {
+        long long v = base + lane;
+        bool live = false;
+        if (v < g.n) {
+            live = g.hs[v].x != -1;
+            if (live) {
+                P.dcur[v] = g.deg[v];
+                g.hs[v].x = UNPEELED;
+            }
+        }
+        warp_push(&C->pc[1], P.L0, ~0ull, live, (int32_t)v);
+    }
+    if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+    unsigned long long nl = vload64(&C->spc[1]);
+    int32_t* Lc = P.L0;
+    int32_t* Ln = P.L1;
+    int k = 0;
+    unsigned long long ft = 0;
+    long long levels = 0;
+    while (nl > 0) {
+        // scan the remaining list
+        const unsigned long long f0 = ft;
+        int mx = 0;   // max of (INT_MAX - degree) over survivors: gives the min degree
+        for (long long base = gwarp * 32; base < (long long)nl; base += nwarps * 32) {
+            long long i = base + lane;
+            bool peel = false, keep = false;
+            int v = 0;
+            if (i < (long long)nl) {
+                v = Lc[i];
+                if (g.hs[v].x == UNPEELED) {
+                    int d = P.dcur[v];
+                    if (d <= k) {
+                        g.hs[v].x = k;
+                        peel = true;
+                    } else {
+                        keep = true;
+                        mx = max(mx, 0x7FFFFFFF - d);
+                    }
+                }
+            }
+            warp_push(&C->tail[0], P.F, ~0ull, peel, v);
+            warp_push(&C->pc[1], Ln, ~0ull, keep, v);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx) atomicMax(&C->pc[3], (unsigned long long)mx);
+        if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+        unsigned long long fhi = vload64(&C->stail[0]);
+        unsigned long long nln = vload64(&C->spc[1]);
+        unsigned long long smx = vload64(&C->spc[3]);
+        int32_t* t = Lc;
+        Lc = Ln;
+        Ln = t;
+        nl = nln;
+        if (fhi == f0) {
+            if (nl == 0) break;
+            k = 0x7FFFFFFF - (int)smx;   // jump to the smallest remaining degree
+            continue;
+        }
+        // sub-waves at level k
+        unsigned long long lo = f0, hi = fhi;
+        while (hi > lo) {
+            const unsigned long long cnt = hi - lo;
+            for (;;) {
+                unsigned long long j = 0;
+                if (lane == 0) j = atomicAdd(&C->pc[2], 1ull);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                if (j >= cnt) break;
+                int v = P.F[lo + j];
+                long long o = g.off[v];
+                int len = g.end[v];
+                for (int t0 = 0; t0 < len; t0 += 32) {
+                    int tt = t0 + lane;
+                    int w = tt < len ? g.adj[o + tt] : HOLE;
+                    bool p = false;
+                    if (w >= 0 && g.hs[w].x == UNPEELED) {
+                        if (atomicSub(&P.dcur[w], 1) == k + 1) {
+                            g.hs[w].x = k;
+                            p = true;
+                        }
+                    }
+                    warp_push(&C->tail[0], P.F, ~0ull, p, w);
+                }
+            }
+            if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+            lo = hi;
+            hi = vload64(&C->stail[0]);
+        }
+        ft = hi;
+        k++;
+        levels++;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_LEVELS] = (unsigned long long)levels;
+}
+
+int peel_blocks_per_sm(int threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, peel_kernel, threads, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_peel(const PeelParams& p, int blocks, int threads, cudaStream_t s) {
+    PeelParams q = p;
+    void* args[] = {&q};
+    return cudaLaunchCooperativeKernel((const void*)peel_kernel, dim3(blocks), dim3(threads), args, 0, s);
+}
+
+// ------------------------------------------------------------------ index rehash
+__global__ void rehash_kernel(const Bucket* __restrict__ old_idx, unsigned long long old_size, DevGraph g, Ctl* c) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)old_size) return;
+    Bucket b = old_idx[i];
+    if (b.key == KEY_EMPTY || b.key == KEY_TOMB) return;
+    bool existed = false;
+    long long nb = idx_insert(g.idx, g.idx_mask, b.key, &existed);
+    if (nb < 0) { atomicCAS(&c->error, 0, E_INDEX_FULL); return; }
+    g.idx[nb].slo = b.slo;
+    g.idx[nb].shi = b.shi;
+}
+
+cudaError_t rehash(const Bucket* old_idx, unsigned long long old_size, DevGraph g, Ctl* c, cudaStream_t s) {
+    if (old_size == 0) return cudaSuccess;
+    rehash_kernel<<<grid_for((long long)old_size, 256, 1ll << 31), 256, 0, s>>>(old_idx, old_size, g, c);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ vertex insertion
+// Neighbour lists of `count` new vertices (ids base..base+count-1): every
+// neighbour is live or new, and not the vertex itself.  Warp per vertex.
+__global__ void validate_vertices_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ nb, int32_t count,
+                                         int32_t base, DevGraph g, Ctl* c) {
+    long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int lane = lane_id();
+    for (; w < count; w += nw) {
+        long long a = off[w], b = off[w + 1];
+        if (a < 0 || b < a) {
+            if (lane == 0) atomicCAS(&c->error, 0, E_INVALID);
+            continue;
+        }
+        for (long long j = a + lane; j < b; j += 32) {
+            int32_t x = nb[j];
+            bool bad = x < 0 || x >= base + count || x == base + w || (x < base && g.hs[x].x < 0);
+            if (bad) {
+                atomicMin(&c->bad_index, j);
+                atomicCAS(&c->error, 0, E_INVALID);
+            }
+        }
+    }
+}
+
+__global__ void init_vertices_kernel(const int64_t* __restrict__ off, int32_t count, int32_t base, DevGraph g, Ctl* c) {
+    long long b0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    int lane = lane_id();
+    for (; b0 < count; b0 += stride) {
+        long long i = b0 + lane;
+        int cp = 0;
+        if (i < count) cp = cap_for(off[i + 1] - off[i], g.slack_pct, g.min_cap);
+        int incl = cp;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long wb = 0;
+        if (lane == 31) wb = atomicAdd(&c->adj_top, (unsigned long long)tot);
+        wb = __shfl_sync(0xffffffffu, wb, 31);
+        if (i < count) {
+            long long v = base + i;
+            g.off[v] = (int64_t)(wb + incl - cp);
+            g.cap[v] = cp;
+            g.end[v] = 0;
+            g.deg[v] = 0;
+            g.hs[v] = make_int4(0, 0, 0, 0);
+            g.chg[v] = 0;
+            g.taken[v] = 0;
+            g.claim0[v] = CLAIM_FREE;
+            g.claim1[v] = CLAIM_FREE;
+            g.need[v] = 0;
+        }
+    }
+}
+
+__global__ void expand_vertex_edges_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ nb,
+                                           int32_t count, int32_t base, int32_t* E) {
+    long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int lane = lane_id();
+    for (; w < count; w += nw) {
+        for (long long j = off[w] + lane; j < off[w + 1]; j += 32) {
+            E[2 * j] = base + (int32_t)w;
+            E[2 * j + 1] = nb[j];
+        }
+    }
+}
+
+cudaError_t validate_vertices(const int64_t* nbr_off, const int32_t* nbrs, int32_t count, int32_t base, DevGraph g,
+                              Ctl* c, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    validate_vertices_kernel<<<grid_for((long long)count * 32, 256, 65536), 256, 0, s>>>(nbr_off, nbrs, count, base, g, c);
+    return cudaGetLastError();
+}
+cudaError_t init_vertices(const int64_t* nbr_off, int32_t count, int32_t base, DevGraph g, Ctl* c, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    init_vertices_kernel<<<grid_for(count, 256, 65536), 256, 0, s>>>(nbr_off, count, base, g, c);
+    return cudaGetLastError();
+}
+cudaError_t expand_vertex_edges(const int64_t* nbr_off, const int32_t* nbrs, int32_t count, int32_t base, int32_t* E,
+                                cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    expand_vertex_edges_kernel<<<grid_for((long long)count * 32, 256, 65536), 256, 0, s>>>(nbr_off, nbrs, count, base, E);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ vertex deletion
+__global__ void validate_ids_kernel(const int32_t* __restrict__ ids, int32_t count, DevGraph g, Ctl* c) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int32_t v = ids[i];
+    if (v < 0 || v >= g.n || g.hs[v].x < 0) {
+        atomicMin(&c->bad_index, i);
+        atomicCAS(&c->error, 0, E_INVALID);
+        return;
+    }
+    atomicAdd(&c->reloc_need, (unsigned long long)g.end[v]);   // upper bound on incident edges
+}
+
+__global__ void gather_incident_kernel(const int32_t* __restrict__ ids, int32_t count, DevGraph g, int2* E,
+                                       long long cap, Ctl* c) {
+    long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int lane = lane_id();
+    for (; w < count; w += nw) {
+        int v = ids[w];
+        long long o = g.off[v];
+        int len = g.end[v];
+        for (int t0 = 0; t0 < len; t0 += 32) {
+            int t = t0 + lane;
+            int x = t < len ? g.adj[o + t] : HOLE;
+            bool live = x >= 0;
+            unsigned int b = __ballot_sync(0xffffffffu, live);
+            unsigned long long base = 0;
+            if (lane == 0 && b) base = atomicAdd(&c->gather_n, (unsigned long long)__popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            long long p = (long long)base + __popc(b & ((1u << lane) - 1));
+            if (live && p < cap) E[p] = make_int2(v, x);
+        }
+    }
+}
+
+__global__ void mark_dead_kernel(const int32_t* __restrict__ ids, int32_t count, DevGraph g) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int32_t v = ids[i];
+    g.hs[v] = make_int4(-1, 0, 0, 0);
+    g.end[v] = 0;
+    g.deg[v] = 0;
+}
+
+cudaError_t validate_ids(const int32_t* ids, int32_t count, DevGraph g, Ctl* c, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    validate_ids_kernel<<<grid_for(count, 256), 256, 0, s>>>(ids, count, g, c);
+    return cudaGetLastError();
+}
+cudaError_t gather_incident(const int32_t* ids, int32_t count, DevGraph g, int32_t* E, long long cap, Ctl* c,
+                            cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    gather_incident_kernel<<<grid_for((long long)count * 32, 256, 65536), 256, 0, s>>>(ids, count, g, (int2*)E, cap, c);
+    return cudaGetLastError();
+}
+cudaError_t mark_dead(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    mark_dead_kernel<<<grid_for(count, 256), 256, 0, s>>>(ids, count, g);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ export
+__global__ void export_cores_kernel(DevGraph g, int32_t* out) {
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n) return;
+    out[v] = g.hs[v].x;
+}
+
+__global__ void export_edges_kernel(DevGraph g, int2* out, Ctl* c) {
+    long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int lane = lane_id();
+    for (; w < g.n; w += nw) {
+        long long o = g.off[w];
+        int len = g.end[w];
+        for (int t0 = 0; t0 < len; t0 += 32) {
+            int t = t0 + lane;
+            int x = t < len ? g.adj[o + t] : HOLE;
+            bool p = x > (int)w;
+            unsigned int b = __ballot_sync(0xffffffffu, p);
+            unsigned long long base = 0;
+            if (lane == 0 && b) base = atomicAdd(&c->gather_n, (unsigned long long)__popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (p) out[base + __popc(b & ((1u << lane) - 1))] = make_int2((int)w, x);
+        }
+    }
+}
+
+cudaError_t export_cores(DevGraph g, int32_t* out, cudaStream_t s) {
+    if (g.n <= 0) return cudaSuccess;
+    export_cores_kernel<<<grid_for(g.n, 256, 1ll << 31), 256, 0, s>>>(g, out);
+    return cudaGetLastError();
+}
+cudaError_t export_edges(DevGraph g, int32_t* out, Ctl* c, cudaStream_t s) {
+    if (g.n <= 0) return cudaSuccess;
+    export_edges_kernel<<<grid_for((long long)g.n * 32, 256, 65536), 256, 0, s>>>(g, (int2*)out, c);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ multi-graph helpers
+// Local ids of a concatenated per-graph batch -> global ids.  prefix[i] is
+// the first batch entry of graph i (ng+1 entries).
+__global__ void localize_multi_kernel(int32_t* E, long long k, const long long* __restrict__ prefix,
+                                      const int32_t* __restrict__ bases, int32_t ng) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {                 // last graph whose prefix <= i
+        int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    int b = bases[lo];
+    int nv = bases[lo + 1] - b;       // bases has ng+1 entries
+    int32_t u = E[2 * i], v = E[2 * i + 1];
+    // an id outside its graph stays invalid (negative) so ingest rejects it
+    E[2 * i] = (u >= 0 && u < nv) ? u + b : -1;
+    E[2 * i + 1] = (v >= 0 && v < nv) ? v + b : -1;
+}
+
+__global__ void count_multi_kernel(const REdge* __restrict__ R, long long n, const int32_t* __restrict__ bases,
+                                   int32_t ng, unsigned long long* per_graph) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int x = R[i].lo;
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (bases[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    atomicAdd(&per_graph[lo], 1ull);
+}
+
+cudaError_t localize_multi(int32_t* E, long long k, const long long* prefix, const int32_t* bases, int32_t ng,
+                           cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    localize_multi_kernel<<<grid_for(k, 256, 1ll << 31), 256, 0, s>>>(E, k, prefix, bases, ng);
+    return cudaGetLastError();
+}
+cudaError_t count_multi(const REdge* R, long long n, const int32_t* bases, int32_t ng, unsigned long long* per_graph,
+                        cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    count_multi_kernel<<<grid_for(n, 256, 1ll << 31), 256, 0, s>>>(R, n, bases, ng, per_graph);
+    return cudaGetLastError();
+}
+
+// capacity totals for a vertex range: sum_only pass of offsets_kernel
+cudaError_t sum_caps(DevGraph g, int32_t v0, int32_t v1, Ctl* c, cudaStream_t s) {
+    if (v1 <= v0) return cudaSuccess;
+    offsets_kernel<<<grid_for(v1 - v0, 256, 65536), 256, 0, s>>>(g, v0, v1, c, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace cm

@@ -14,7 +14,7 @@ What pins what:
   * traversal (O3) and    BZ after every single edge / every batch, the
     batched method (O4)   golden fixtures, and per-iteration invariants of
                           Section IV: selection is a superior edge set
-                          (Definition 3 (ii) at every level) and maximal,
+                          (Definition 6 (ii) at every level) and maximal,
                           cores move by at most one per iteration (Lemmas 3-4)
                           and only at the levels of the selected edges
                           (Lemmas 1-2 (ii)), insertion never lowers and
@@ -238,7 +238,7 @@ def run_batch_with_invariants(og, op, batch, plant=0):
             cons, k = _constrained(before, u, v)
             levels.add(k)
             for x in cons:
-                assert x not in taken, "Definition 3 (ii): one edge per constrained endpoint"
+                assert x not in taken, "Definition 6 (ii): one edge per constrained endpoint"
                 taken[x] = (u, v)
         remset -= selk
         for u, v in remset:
