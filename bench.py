@@ -1,0 +1,363 @@
+"""Benchmark: batched k-core maintenance on one or more GB300s.
+
+Workload (one "step" = one round of the R-MAT scale-20 stream): R-MAT
+(a,b,c,d) = (.57,.19,.19,.05), 2^20 vertices, 16 * 2^20 sampled edges
+(symmetrised, deduplicated, ids permuted); each round inserts 10^4 uniform
+new edges, deletes 10^4 uniform existing edges, inserts 100 vertices of
+degree 8 and deletes 100 uniform live vertices, each as one batched call.
+
+value: edge updates applied per second over K timed rounds, inputs already
+in device memory, device time by CUDA events on the handle's stream, L2
+flushed (256 MiB write) before every round.  e2e: the same metric through
+host (pinned) buffers, copies inside the timed region, and the full core
+array read back after every round.  roofline: the maintenance kernel's
+algorithmic bytes over its event-timed duration against the measured HBM
+copy bandwidth.  cpu_baseline / --impl reference: the CPU oracle (the
+paper's sequential single-edge traversal) on a bounded prefix of the
+same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: torchrun, one rank per GPU, every rank runs its own replica.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge updates/sec (insert & delete)"
+UNIT = "edge updates/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the maintenance kernel from the committed ncu
+    summary, only if the kernel source is unchanged since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "maintain_traffic.json")) as f:
+            t = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1612_09368_gb300", "csrc", "cm_maintain.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != t.get("source_sha"):
+            return None
+        return t.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sms, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(args, rounds):
+    from synth import workloads
+    return workloads.rmat_rounds(rounds, scale=args.scale)
+
+
+def config_of(w, args):
+    c = {"workload": w.name, **w.params, "vertices": w.n, "initial_edges": int(len(w.edges)),
+         "l2": "flushed before every step (256 MiB write)", "parallelism": "replicas"}
+    return c
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def cpu_oracle_rate(w, budget_s: float):
+    """Edges/s of the paper's sequential single-edge traversal (oracle O3) on
+    a prefix of round 0's insert and delete batches, ~budget_s seconds."""
+    import oracle
+    og = oracle.OracleGraph(w.n, w.edges, mode=oracle.SEQUENTIAL)
+    done, t_used = 0, 0.0
+    for r in w.rounds:
+        t0 = time.perf_counter()
+        done += og.insert_edges(r.ins)
+        done += og.delete_edges(r.dele)
+        og.insert_vertices(r.vnbrs.tolist())
+        done += r.vnbrs.size
+        done += og.delete_vertices(r.vdel)
+        t_used += time.perf_counter() - t0
+        if t_used >= budget_s:
+            break
+    return done / t_used, done, t_used
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    w = make_workload(args, 8)
+    per = []
+    total_edges = 0
+    total_t = 0.0
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for s in range(args.warmup + args.steps):
+        rate, edges, t = cpu_oracle_rate(w, budget)
+        if s >= args.warmup:
+            per.append(rate)
+            total_edges += edges
+            total_t += t
+    value = total_edges / total_t if total_t else 0.0
+    sample = (f"whole rounds from round 0 of {w.name} until ~{budget:.0f} s per step, "
+              "oracle O3 sequential single-edge traversal, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": config_of(w, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_round(g, r, dev_inputs, cm):
+    """One step: the four batched calls of a round.  Returns (edge updates,
+    stats of each call)."""
+    ins, dele, off, nb, vd = dev_inputs
+    st = []
+    a = g.insert_edges(ins)
+    st.append(g.stats())
+    b = g.delete_edges(dele)
+    st.append(g.stats())
+    first, c = cm.cm_insert_vertices(g.handle, off, nb)
+    st.append(g.stats())
+    d = g.delete_vertices(vd)
+    st.append(g.stats())
+    return a + b + c + d, st
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1612_09368_gb300 as cm
+    from paper_1612_09368_gb300 import build as libbuild
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    libbuild.build()
+    K, W = args.steps, args.warmup
+    e2e_rounds = 0 if args.no_e2e else K
+    w = make_workload(args, W + K + e2e_rounds)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    g = cm.CoreGraph(w.n, torch.from_numpy(w.edges).to(dev), stream=stream)
+
+    def to_dev(r):
+        off = np.zeros(len(r.vnbrs) + 1, np.int64)
+        off[1:] = np.cumsum([r.vnbrs.shape[1]] * len(r.vnbrs))
+        return (torch.from_numpy(r.ins).to(dev), torch.from_numpy(r.dele).to(dev), torch.from_numpy(off).to(dev),
+                torch.from_numpy(np.ascontiguousarray(r.vnbrs.ravel())).to(dev), torch.from_numpy(r.vdel).to(dev))
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+
+    # warm-up rounds
+    for s in range(W):
+        run_round(g, w.rounds[s], to_dev(w.rounds[s]), cm)
+    dev_in = [to_dev(w.rounds[W + s]) for s in range(K)]
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    torch.cuda.synchronize()
+    units = 0
+    maint_ms = 0.0
+    alg_bytes = 0
+    maint_launches = 0
+    launches = 0
+    iters = []
+    per_call_ms = {"insert": [], "delete": [], "vinsert": [], "vdelete": []}
+    for s in range(K):
+        flush.fill_(s)
+        ev0[s].record(stream)
+        u, st = run_round(g, w.rounds[W + s], dev_in[s], cm)
+        ev1[s].record(stream)
+        units += u
+        for name, x in zip(per_call_ms, st):
+            per_call_ms[name].append(x["call_ms"])
+            maint_ms += x["maintain_ms"]
+            alg_bytes += x["alg_bytes"]
+            launches += x["launches"]
+            maint_launches += 1 if x["maintain_ms"] > 0 else 0
+            iters.append(x["iterations"])
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t_ms = sum(ev0[s].elapsed_time(ev1[s]) for s in range(K))
+    if ws > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        uu = torch.tensor([units], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+        t_ms, units_all = float(tt.item()), float(uu.item())
+    else:
+        units_all = units
+    value = units_all / (t_ms / 1000.0)
+
+    # e2e: host pinned inputs, copies and the core read-back inside the timed region
+    e2e = None
+    if e2e_rounds:
+        host_in = []
+        for s in range(e2e_rounds):
+            r = w.rounds[W + K + s]
+            off = np.zeros(len(r.vnbrs) + 1, np.int64)
+            off[1:] = np.cumsum([r.vnbrs.shape[1]] * len(r.vnbrs))
+            host_in.append(tuple(torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+                                 for x in (r.ins, r.dele, off, r.vnbrs.ravel(), r.vdel)))
+        out = torch.empty(g.n + 2 * e2e_rounds * 200, dtype=torch.int32).pin_memory()
+        h2d = sum(sum(x.numel() * x.element_size() for x in hi) for hi in host_in) / e2e_rounds
+        e_units = 0
+        e_ms = 0.0
+        d2h = 0
+        for s in range(e2e_rounds):
+            flush.fill_(s)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            u, _ = run_round(g, w.rounds[W + K + s], host_in[s], cm)
+            n_now = g.n
+            g.cores(out[:n_now])
+            a1.record(stream)
+            a1.synchronize()
+            e_ms += a0.elapsed_time(a1)
+            e_units += u
+            d2h += 4 * n_now
+        e2e = {"value": e_units / (e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h / e2e_rounds)}
+
+    # re-peel comparator: apply 10^4 new edges structurally + full GPU peel,
+    # against maintaining the same-size insert batches above
+    repeel = None
+    if rank == 0:
+        from synth import UNIFORM, stream as sstream
+        extra = w.final.sample_insert(10 ** 4, UNIFORM, sstream(2, 0, 10 ** 6, 1))
+        xin = torch.from_numpy(extra).to(dev)
+        torch.cuda.synchronize()
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        r0.record(stream)
+        g.apply_edges(cm.CM_OP_INSERT, xin)
+        g.recompute_cores()
+        r1.record(stream)
+        r1.synchronize()
+        rp_ms = r0.elapsed_time(r1)
+        mi = statistics.median(per_call_ms["insert"])
+        repeel = {"repeel_ms": rp_ms, "maintain_insert_1e4_ms_median": mi, "speedup": rp_ms / mi,
+                  "peel_levels": g.stats()["peel_levels"]}
+
+    peak, peak_kind = load_peaks()
+    achieved = alg_bytes / (maint_ms / 1000.0) / 1e9 if maint_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": kernel_traffic(), "peak_kind": peak_kind,
+                "kernel": "maintain_kernel",
+                "alg_bytes_per_launch": alg_bytes / max(1, maint_launches),
+                "avg_launch_ms": maint_ms / max(1, maint_launches)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, edges, t = cpu_oracle_rate(w, args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{edges} edge updates (whole rounds from round 0), {t:.1f} s, "
+                         "oracle O3 sequential single-edge traversal, 1 thread"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+                "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic", "config": config_of(w, args),
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "cpu_baseline": cpu, "repeel": repeel,
+                "detail": {"iterations_per_call_mean": float(np.mean(iters)),
+                           "call_ms_median": {k: statistics.median(v) for k, v in per_call_ms.items()},
+                           "maintain_ms_total": maint_ms, "units": units_all}}
+        print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -432,12 +432,13 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     CK(h, cudaMemset(h->ctl, 0, sizeof(Ctl)));
     CK(h, cudaMallocHost(&h->hctl, sizeof(Ctl)));
     memset(h->hctl, 0, sizeof(Ctl));
-    h->g.n = n;
     h->g.slack_pct = h->opt.slack_pct;
     h->g.min_cap = h->opt.min_cap;
-    h->n = n;
+    h->n = 0;                                  // grow_vertices keeps (and does not clear) [0, n)
     int rc = grow_vertices(h, n > 0 ? n : 1);
     if (rc) return rc;
+    h->n = n;
+    h->g.n = n;
     if ((rc = alloc_index(h, pow2_at_least((unsigned long long)(2 * m + m / 2 + 1024))))) return rc;
     const int32_t* dE = edges;
     int32_t* tmp = nullptr;

@@ -318,6 +318,10 @@ def test_multi_graph_one_launch(cm):
     assert bases.tolist() == np.concatenate([[0], np.cumsum(ns)[:-1]]).tolist()
     refs = [oracle.OracleGraph(ns[i], parts[i], mode=oracle.SUPERIOR) for i in range(ng)]
     dyns = [synth.DynGraph(ns[i], parts[i]) for i in range(ng)]
+    # the union with global ids: priorities hash global keys, so the union's
+    # oracle run gives the exact iteration count of the fused call
+    union = oracle.OracleGraph(int(sum(ns)), np.concatenate([p + b for p, b in zip(parts, bases)]),
+                               mode=oracle.SUPERIOR)
     for op in (0, 1):
         batches = []
         for i in range(ng):
@@ -328,13 +332,14 @@ def test_multi_graph_one_launch(cm):
                 batches.append(dyns[i].sample_delete(b, synth.UNIFORM, synth.stream(52, i)))
         counts = [len(b) for b in batches]
         per = g.update_multi(op, counts, _dev(np.concatenate(batches)))
-        iters = 0
         for i in range(ng):
             exp = refs[i].insert_edges(batches[i]) if op == 0 else refs[i].delete_edges(batches[i])
             dyns[i].apply(op, batches[i])
             assert per[i] == exp
-            iters = max(iters, refs[i].last_iterations())
-        assert g.stats()["iterations"] == iters
+        glob = np.concatenate([b + bases[i] for i, b in enumerate(batches)])
+        (union.insert_edges if op == 0 else union.delete_edges)(glob)
+        assert g.stats()["iterations"] == union.last_iterations()
+        assert (g.cores() == union.cores()).all()
         c = g.cores()
         for i in range(ng):
             assert (c[bases[i]: bases[i] + ns[i]] == refs[i].cores()).all(), (op, i)
