@@ -250,6 +250,10 @@ def main():
     launches = 0
     iters = []
     per_call_ms = {"insert": [], "delete": [], "vinsert": [], "vdelete": []}
+    per_call_it = {k: [] for k in per_call_ms}
+    per_call_grid_it = {k: 0 for k in per_call_ms}
+    per_call_bar = {k: 0 for k in per_call_ms}
+    phase_ns = {}
     for s in range(K):
         flush.fill_(s)
         ev0[s].record(stream)
@@ -258,6 +262,11 @@ def main():
         units += u
         for name, x in zip(per_call_ms, st):
             per_call_ms[name].append(x["call_ms"])
+            per_call_it[name].append(x["iterations"])
+            per_call_grid_it[name] += x["grid_iterations"]
+            per_call_bar[name] += x["barriers"]
+            for ph, ns in x["phase_ns"].items():
+                phase_ns[ph] = phase_ns.get(ph, 0) + ns
             maint_ms += x["maintain_ms"]
             alg_bytes += x["alg_bytes"]
             launches += x["launches"]
@@ -351,6 +360,10 @@ def main():
                 "cpu_baseline": cpu, "repeel": repeel,
                 "detail": {"iterations_per_call_mean": float(np.mean(iters)),
                            "call_ms_median": {k: statistics.median(v) for k, v in per_call_ms.items()},
+                           "call_ms_mean": {k: float(np.mean(v)) for k, v in per_call_ms.items()},
+                           "iterations_mean": {k: float(np.mean(v)) for k, v in per_call_it.items()},
+                           "grid_iterations": per_call_grid_it, "barriers": per_call_bar,
+                           "phase_ms": {k: v / 1e6 for k, v in phase_ns.items()},
                            "maintain_ms_total": maint_ms, "units": units_all}}
         print(json.dumps(line), flush=True)
     g.close()

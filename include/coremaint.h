@@ -103,7 +103,10 @@ typedef struct cm_stats {
     double maintain_ms;      /* device time of the maintenance kernel (CUDA events on the handle's stream) */
     double call_ms;          /* device time of the whole call, first copy to last kernel */
     int64_t peel_levels;     /* cm_recompute_cores / cm_create: peeling levels */
-    int64_t reserved[7];
+    int64_t barriers;        /* barriers executed by the maintenance launches */
+    int64_t grid_iterations; /* iterations run grid-wide (the rest ran in one block) */
+    int64_t phase_ns[7];     /* device time per phase: claim, check, apply, discover, evict, commit, fix-up */
+    int64_t reserved[4];
 } cm_stats;
 
 /* Fills *opt with the defaults. */

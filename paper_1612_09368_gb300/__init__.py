@@ -58,10 +58,15 @@ class cm_stats(ctypes.Structure):
         "applied", "iterations", "select_rounds", "selected", "remaining_sum", "visited", "visited_slots",
         "evicted", "evicted_slots", "changed", "changed_slots", "waves", "alg_bytes", "launches")] + [
         ("maintain_ms", ctypes.c_double), ("call_ms", ctypes.c_double), ("peel_levels", ctypes.c_int64),
-        ("reserved", ctypes.c_int64 * 7)]
+        ("barriers", ctypes.c_int64), ("grid_iterations", ctypes.c_int64), ("phase_ns", ctypes.c_int64 * 7),
+        ("reserved", ctypes.c_int64 * 4)]
+
+    PHASES = ("claim", "check", "apply", "discover", "evict", "commit", "fixup")
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "phase_ns")}
+        d["phase_ns"] = dict(zip(self.PHASES, list(self.phase_ns)))
+        return d
 
 
 class CoreMaintError(RuntimeError):

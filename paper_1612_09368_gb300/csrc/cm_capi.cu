@@ -61,6 +61,8 @@ struct cm_graph {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cm_stats last{};
     long long launches = 0;
+    // execution-mode thresholds of the maintenance kernel (see cm_iterate.cu)
+    long long small_edges = 1024, small_work = 2048, big_work = 16384;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -619,26 +621,51 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         p.ctl = h->ctl;
         p.R0 = h->R0;
         p.R1 = h->R1;
-        p.nrem0 = (unsigned long long)nrem0;
         p.VQ = h->VQ;
         p.EQ = h->EQ;
         p.CQ = h->CQ;
         p.qmask = h->qmask;
-        p.epoch0 = h->epoch;
         p.op = op;
         p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
         p.max_iters = nrem0 + 1;
+        p.small_edges = h->small_edges;
+        p.small_work = h->small_work;
+        p.big_work = h->big_work;
         int blocks, threads;
         persistent_geometry(h, 0, nrem0, &blocks, &threads);
         p.expect = (uint32_t)blocks;
-        if (h->opt.debug_flags & CM_DEBUG_BARRIER_NEVER_RELEASES) {
-            p.expect = (uint32_t)blocks + 1;   // test hook: no barrier can complete
+        bool debug_hang = (h->opt.debug_flags & CM_DEBUG_BARRIER_NEVER_RELEASES) != 0;
+        if (debug_hang) {
+            p.expect = (uint32_t)blocks + 1;   // test hook: no grid barrier can complete
+            p.small_edges = -1;                // and the grid mode must run
             h->opt.debug_flags &= ~CM_DEBUG_BARRIER_NEVER_RELEASES;
         }
+        // where the call starts: all kept edges remain, in R0
+        Resume rs{};
+        rs.nrem = (unsigned long long)nrem0;
+        rs.rsel = 0;
+        rs.epoch = h->epoch;
+        rs.done = 0;
+        rs.want = (!debug_hang && nrem0 <= h->small_edges) ? 1 : 0;
+        rs.iters = 0;
+        h->hctl->rs = rs;
+        CK(h, cudaMemcpyAsync(&h->ctl->rs, &h->hctl->rs, sizeof(Resume), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaEventRecord(h->ev[2], h->stream));
-        LAUNCH(h, launch_maintain(p, blocks, threads, h->stream));
+        // grid launch then block launch: whichever the resume state names runs,
+        // the other returns at once; a handover inside the pair needs no host.
+        bool want_grid = rs.want == 0;
+        for (int pass = 0;; pass++) {
+            if (pass >= 256) {
+                h->poisoned = true;
+                return set_err(h, CM_ERR_LIMIT, "maintenance did not finish within 256 launch pairs");
+            }
+            if (want_grid) LAUNCH(h, launch_maintain(p, blocks, threads, h->stream));
+            LAUNCH(h, launch_maintain_block(p, 1024, h->stream));
+            if ((rc = rd_ctl(h))) return rc;
+            if (c.error || c.rs.done) break;
+            want_grid = c.rs.want == 0;
+        }
         CK(h, cudaEventRecord(h->ev[3], h->stream));
-        if ((rc = rd_ctl(h))) return rc;
         if (c.error) {
             h->poisoned = true;
             const char* why = c.error == E_BARRIER_TIMEOUT ? "a grid barrier wait ran out"
@@ -647,7 +674,8 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
                                                           : "device error";
             return set_err(h, CM_ERR_LIMIT, "maintenance stopped: %s (code %d)", why, c.error);
         }
-        h->epoch = (uint32_t)c.wc;
+        CK(h, cudaEventSynchronize(h->ev[3]));
+        h->epoch = c.rs.epoch;
         float ms = 0;
         cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
         cm_stats& s = h->last;
@@ -663,6 +691,9 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         s.changed += (int64_t)c.st[ST_CHANGED];
         s.changed_slots += (int64_t)c.st[ST_CHSLOTS];
         s.waves += (int64_t)c.st[ST_WAVES];
+        s.barriers += (int64_t)c.st[ST_BARRIERS];
+        s.grid_iterations += (int64_t)c.st[ST_GRID_ITERS];
+        for (int i = 0; i < PH_COUNT && i < 7; i++) s.phase_ns[i] += (int64_t)c.ph[i];
         // Algorithmic bytes of the maintenance launch: per iteration 16 B per
         // remaining edge (pair + both cores) and 16 B per selected edge
         // (claims, CSR writes); 16 B per visited vertex (its row) plus 12 B

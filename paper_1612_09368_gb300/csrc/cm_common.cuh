@@ -51,7 +51,22 @@ constexpr uint32_t F_SEL = 1u, F_BLK = 2u;
 // Stats slots (Ctl::st)
 enum {
     ST_ITERS = 0, ST_ROUNDS, ST_SELECTED, ST_REMSUM, ST_VISITED, ST_VISSLOTS, ST_EVICTED, ST_EVSLOTS,
-    ST_CHANGED, ST_CHSLOTS, ST_WAVES, ST_LEVELS, ST_COUNT
+    ST_CHANGED, ST_CHSLOTS, ST_WAVES, ST_LEVELS, ST_BARRIERS, ST_GRID_ITERS, ST_COUNT
+};
+// Phase ids of the per-phase timers (Ctl::ph)
+enum { PH_CLAIM = 0, PH_CHECK, PH_APPLY, PH_DISCOVER, PH_EVICT, PH_COMMIT, PH_FIXUP, PH_COUNT };
+
+// Where a maintenance launch resumes: written by the host before the first
+// launch of a call and by a kernel that hands the call over to the other
+// execution mode (grid-wide or single-block) at an iteration boundary.
+struct Resume {
+    unsigned long long nrem;   // remaining edges
+    uint32_t rsel;             // which remaining-edge buffer holds them
+    uint32_t epoch;            // next iteration's stamp
+    int done;                  // every edge applied
+    int want;                  // 0: grid mode next, 1: single-block mode next
+    long long iters;           // iterations so far (for the cap)
+    long long pad;
 };
 
 // Device control block, one per handle.  The barrier words and counters are
@@ -66,6 +81,7 @@ struct __align__(128) Ctl {
     unsigned long long stail[4];   // snapshot of tail at the last barrier
     unsigned long long spc[4];     // snapshot of pc at the last barrier
     unsigned long long st[ST_COUNT];
+    unsigned long long ph[PH_COUNT];   // nanoseconds per phase (block 0's view)
     // ingest / host exchange
     unsigned long long nrem;       // edges kept by ingest
     unsigned long long noverflow;  // vertices whose capacity the batch exceeds
@@ -76,6 +92,7 @@ struct __align__(128) Ctl {
     int min_deg;                   // peel: smallest remaining degree
     int pad0;
     unsigned long long wc;         // spare
+    Resume rs;
 };
 
 // Plain-old-data view of a graph passed to kernels by value.
@@ -190,6 +207,23 @@ __device__ __forceinline__ bool grid_sync(Ctl* c, unsigned int expect, unsigned 
             }
         }
         __threadfence();
+        s_ok = vload32(&c->error) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The same contract for a launch of one block: __syncthreads is the
+// barrier and thread 0 takes the snapshots.
+__device__ __forceinline__ bool block_sync(Ctl* c) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; i++) {
+            c->stail[i] = vload64(&c->tail[i]);
+            c->spc[i] = vload64(&c->pc[i]);
+            c->pc[i] = 0;
+        }
         s_ok = vload32(&c->error) == 0;
     }
     __syncthreads();

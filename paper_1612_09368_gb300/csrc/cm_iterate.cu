@@ -1,0 +1,528 @@
+// cm_iterate.cu -- the superior-edge-set iterations of one update batch.
+//
+// maintain_kernel<MODE> runs the iterations of SuperiorEdgeInsert
+// (Algorithm 1) or SuperiorEdgeDelete (Algorithm 5) on the remaining edges
+// of a batch.  MODE 0 is a cooperative launch filling the GPU, with grid-wide
+// barriers; MODE 1 is one block of 1024 threads with __syncthreads barriers,
+// for the long tail of iterations that carry little work (a barrier there
+// costs ~0.1 us instead of a few us).  Either kernel stops at an iteration
+// boundary when the other mode suits the work better and records where to
+// resume (Ctl::rs); the host queues a grid launch and a block launch back to
+// back, so the handover needs no host round trip.
+//
+// Each iteration:
+//   SELECT   a maximal superior edge set (Section IV, Definition 6 and the
+//            union after it; Algorithm 2 made deterministic).  An edge's
+//            constrained endpoints are those whose core equals the edge's
+//            core number min(core(u), core(v)).  In claim rounds every
+//            eligible edge writes its priority fmix64(key) into its
+//            constrained endpoints with atomicMin and wins when it holds all
+//            of them; winners take their endpoints and edges touching a taken
+//            endpoint wait for the next iteration.  The result is the greedy
+//            (lexicographically first) maximal set in priority order.
+//   APPLY    insert / delete the selected edges in the slack CSR and move
+//            SD (superior degree, Definition 7) of constrained endpoints.
+//   insert:  DISCOVER the candidate sets of all levels at once -- the exKPT
+//            of Definition 10, walked breadth-first from the constrained
+//            endpoints through vertices w with core(w) = k and SD(w) > k,
+//            expanding only from vertices whose CSD (Definition 8) exceeds
+//            k (the positive search of Algorithm 3).  A vertex's support
+//            starts at its CSD.  EVICT in waves: a vertex whose support is
+//            <= k cannot rise (Lemma 8); it takes one support from every
+//            visited core-k neighbour, which leaves when its support falls to
+//            k (InsertRemove, Algorithm 4).  COMMIT: survivors rise by one
+//            (Algorithm 1 line 7, Lemma 7).
+//   delete:  EVICT in waves from the constrained endpoints whose SD fell
+//            below k (Algorithm 6); an evicted vertex drops by one and takes
+//            one from the support (initially SD) of every core-k neighbour,
+//            which leaves when its support falls below k (DeleteRemove,
+//            Algorithm 7; Algorithm 5 line 7).
+//   FIX-UP   recompute SD of moved vertices and adjust SD of unmoved
+//            neighbours whose core equals the moved vertex's new core
+//            (insert) or old core (delete).  It only writes SD, which the
+//            next iteration first reads in APPLY, so it runs inside the next
+//            iteration's first claim phase and costs no barrier of its own.
+// All levels run together on the cores of the iteration's start: discovery
+// and eviction only ever follow neighbours of the vertex's own level.
+#include "cm_common.cuh"
+#include "cm_launch.h"
+
+namespace cm {
+
+struct LocalStats {
+    long long vis = 0, visl = 0, ev = 0, evl = 0, ch = 0, chl = 0, sel = 0;
+};
+
+template <int MODE>
+struct Barrier {
+    Ctl* c;
+    uint32_t expect;
+    unsigned long long limit;
+    unsigned long long t_last;
+    bool timer;
+    __device__ bool operator()(int phase) {
+        bool ok = MODE == 0 ? grid_sync(c, expect, limit) : block_sync(c);
+        if (timer) {
+            unsigned long long now = gtimer();
+            c->ph[phase] += now - t_last;
+            c->st[ST_BARRIERS] += 1;
+            t_last = now;
+        }
+        return ok;
+    }
+};
+
+__device__ __forceinline__ void edge_level(const DevGraph& g, const REdge& E, int& k, bool& clo, bool& chi) {
+    int a = g.hs[E.lo].x, b = g.hs[E.hi].x;
+    k = min(a, b);
+    clo = a == k;
+    chi = b == k;
+}
+
+// Selection, claim phase of round r.
+__device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e) {
+    REdge E = R[i];
+    int k; bool clo, chi;
+    edge_level(g, E, k, clo, chi);
+    uint32_t f = E.flags;
+    if (r > 0 && (f >> 2) == (uint32_t)r) {   // claimed in round r-1: clear that buffer
+        unsigned long long* cb = ((r - 1) & 1) ? g.claim1 : g.claim0;
+        if (clo) cb[E.lo] = CLAIM_FREE;
+        if (chi) cb[E.hi] = CLAIM_FREE;
+    }
+    if (f & (F_SEL | F_BLK)) return;
+    if ((clo && g.taken[E.lo] == e) || (chi && g.taken[E.hi] == e)) {
+        R[i].flags = f | F_BLK;
+        return;
+    }
+    unsigned long long prio = fmix64(ekey(E.lo, E.hi));
+    unsigned long long* cb = (r & 1) ? g.claim1 : g.claim0;
+    if (clo) atomicMin(&cb[E.lo], prio);
+    if (chi) atomicMin(&cb[E.hi], prio);
+    R[i].flags = (f & 3u) | ((uint32_t)(r + 1) << 2);
+}
+
+// Selection, check phase of round r.  Returns 1 if the edge claimed and lost.
+__device__ __forceinline__ int check_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e,
+                                          long long& nsel) {
+    REdge E = R[i];
+    if ((E.flags >> 2) != (uint32_t)(r + 1)) return 0;
+    int k; bool clo, chi;
+    edge_level(g, E, k, clo, chi);
+    unsigned long long prio = fmix64(ekey(E.lo, E.hi));
+    const unsigned long long* cb = (r & 1) ? g.claim1 : g.claim0;
+    bool win = (!clo || cb[E.lo] == prio) && (!chi || cb[E.hi] == prio);
+    if (!win) return 1;
+    R[i].flags = E.flags | F_SEL;
+    if (clo) g.taken[E.lo] = e;
+    if (chi) g.taken[E.hi] = e;
+    nsel++;
+    return 0;
+}
+
+// Warp-per-vertex loop over a ring range with dynamic fetching (pc[2]).
+#define FOR_EACH_VERTEX(C, ring, qm, lo, hi, v)                         \
+    for (;;) {                                                          \
+        unsigned long long j_ = 0;                                      \
+        if (lane == 0) j_ = atomicAdd(&(C)->pc[2], 1ull);               \
+        j_ = __shfl_sync(0xffffffffu, j_, 0);                           \
+        if (j_ >= (hi) - (lo)) break;                                   \
+        const int v = (ring)[((lo) + j_) & (qm)];
+
+#define END_FOR_EACH_VERTEX }
+
+// SD fix-up of the vertices whose core moved in iteration e.
+__device__ __forceinline__ void fixup(const DevGraph& g, Ctl* C, const int32_t* Q, unsigned long long qm,
+                                      unsigned long long lo, unsigned long long hi, uint32_t e, int op,
+                                      LocalStats& ls) {
+    const int lane = lane_id();
+    FOR_EACH_VERTEX(C, Q, qm, lo, hi, v)
+        const int kn = g.hs[v].x;
+        const long long o = g.off[v];
+        const int len = g.end[v];
+        const int adj_core = op == 0 ? kn : kn + 1;   // neighbours whose SD counts v differently now
+        int sd = 0;
+        for (int t = lane; t < len; t += 32) {
+            int w = g.adj[o + t];
+            if (w >= 0) {
+                int cw = g.hs[w].x;
+                sd += cw >= kn;
+                if (cw == adj_core && g.chg[w] != e) {
+                    if (op == 0) atomicAdd(&g.hs[w].y, 1);
+                    else atomicSub(&g.hs[w].y, 1);
+                }
+            }
+        }
+        sd = warp_sum(sd);
+        if (lane == 0) {
+            g.hs[v].y = sd;
+            ls.ch++;
+            ls.chl += len;
+        }
+    END_FOR_EACH_VERTEX
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(MODE == 0 ? 512 : 1024, MODE == 0 ? 2 : 1) maintain_kernel(MaintainParams P) {
+    Ctl* C = P.ctl;
+    const DevGraph g = P.g;
+    // where to resume (host or the other mode wrote it before this launch)
+    const int done0 = *(volatile int*)&C->rs.done;
+    const int want = *(volatile int*)&C->rs.want;
+    if (done0 || want != MODE || vload32(&C->error)) return;
+    const int lane = lane_id();
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long qm = P.qmask;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    Barrier<MODE> sync{C, P.expect, P.limit_ns, gtimer(), leader};
+    const uint32_t rsel0 = *(volatile uint32_t*)&C->rs.rsel;
+    REdge* Rc = rsel0 ? P.R1 : P.R0;
+    REdge* Rn = rsel0 ? P.R0 : P.R1;
+    unsigned long long nrem = vload64(&C->rs.nrem);
+    uint32_t e = *(volatile uint32_t*)&C->rs.epoch;
+    const long long iters0 = *(volatile long long*)&C->rs.iters;
+    unsigned long long vq_t = vload64(&C->tail[0]), eq_t = vload64(&C->tail[1]), cq_t = vload64(&C->tail[2]);
+    LocalStats ls;
+    long long iters = 0, rounds = 0, waves = 0, remsum = 0;
+    bool ok = true;
+    // pending SD fix-up of the previous iteration
+    bool fx = false;
+    unsigned long long fx_lo = 0, fx_hi = 0;
+    uint32_t fx_e = 0;
+    int next_want = MODE, finished = 0;
+
+    while (nrem > 0) {
+        if (iters0 + iters >= P.max_iters) {
+            if (leader) atomicCAS(&C->error, 0, E_ITER_LIMIT);
+            ok = false;
+            break;
+        }
+        remsum += (long long)nrem;
+        // ------------------------------------------------ SELECT
+        int r = 0;
+        for (;;) {
+            if (r == 0 && fx) {
+                fixup(g, C, P.op == 0 ? P.CQ : P.EQ, qm, fx_lo, fx_hi, fx_e, P.op, ls);
+                fx = false;
+            }
+            for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
+                long long i = base + lane;
+                if (i < (long long)nrem) claim_edge(g, Rc, i, r, e);
+            }
+            if (!(ok = sync(PH_CLAIM))) break;
+            int lost = 0;
+            for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
+                long long i = base + lane;
+                if (i < (long long)nrem) lost += check_edge(g, Rc, i, r, e, ls.sel);
+            }
+            lost = warp_sum(lost);
+            if (lane == 0 && lost) atomicAdd(&C->pc[0], (unsigned long long)lost);
+            if (!(ok = sync(PH_CHECK))) break;
+            r++;
+            if (vload64(&C->spc[0]) == 0) break;
+        }
+        if (!ok) break;
+        rounds += r;
+        // ------------------------------------------------ APPLY
+        const unsigned long long vq0 = vq_t, eq0 = eq_t, cq0 = cq_t;
+        for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
+            long long i = base + lane;
+            bool valid = i < (long long)nrem;
+            REdge E = {0, 0, 0, 0};
+            bool sel = false, s_lo = false, s_hi = false;
+            if (valid) {
+                E = Rc[i];
+                int k; bool clo, chi;
+                edge_level(g, E, k, clo, chi);
+                if ((E.flags >> 2) == (uint32_t)r) {     // claimed in the final round
+                    unsigned long long* cb = ((r - 1) & 1) ? g.claim1 : g.claim0;
+                    if (clo) cb[E.lo] = CLAIM_FREE;
+                    if (chi) cb[E.hi] = CLAIM_FREE;
+                }
+                sel = (E.flags & F_SEL) != 0;
+                if (sel) {
+                    if (P.op == 0) {
+                        int pu = atomicAdd(&g.end[E.lo], 1), pv = atomicAdd(&g.end[E.hi], 1);
+                        if (pu < g.cap[E.lo] && pv < g.cap[E.hi]) {
+                            g.adj[g.off[E.lo] + pu] = E.hi;
+                            g.adj[g.off[E.hi] + pv] = E.lo;
+                            g.idx[E.bkt].slo = pu;
+                            g.idx[E.bkt].shi = pv;
+                        } else {
+                            atomicCAS(&C->error, 0, E_CAPACITY);
+                        }
+                        atomicAdd(&g.deg[E.lo], 1);
+                        atomicAdd(&g.deg[E.hi], 1);
+                        if (clo) {
+                            int m = atomicAdd(&g.hs[E.lo].y, 1) + 1;
+                            s_lo = m > k && atomicExch((unsigned int*)&g.hs[E.lo].z, e) != e;
+                        }
+                        if (chi) {
+                            int m = atomicAdd(&g.hs[E.hi].y, 1) + 1;
+                            s_hi = m > k && atomicExch((unsigned int*)&g.hs[E.hi].z, e) != e;
+                        }
+                    } else {
+                        Bucket b = g.idx[E.bkt];
+                        if (b.slo >= 0 && b.slo < g.end[E.lo] && b.shi >= 0 && b.shi < g.end[E.hi]) {
+                            g.adj[g.off[E.lo] + b.slo] = HOLE;
+                            g.adj[g.off[E.hi] + b.shi] = HOLE;
+                        } else {
+                            atomicCAS(&C->error, 0, E_CAPACITY);
+                        }
+                        g.idx[E.bkt].key = KEY_TOMB;
+                        atomicSub(&g.deg[E.lo], 1);
+                        atomicSub(&g.deg[E.hi], 1);
+                        if (clo) {
+                            int m = atomicSub(&g.hs[E.lo].y, 1) - 1;
+                            if (m < k) { s_lo = true; g.chg[E.lo] = e; }
+                        }
+                        if (chi) {
+                            int m = atomicSub(&g.hs[E.hi].y, 1) - 1;
+                            if (m < k) { s_hi = true; g.chg[E.hi] = e; }
+                        }
+                    }
+                }
+                E.flags = 0;
+            }
+            warp_push_edge(&C->pc[1], Rn, valid && !sel, E);
+            unsigned long long* qt = P.op == 0 ? &C->tail[0] : &C->tail[1];
+            int32_t* q = P.op == 0 ? P.VQ : P.EQ;
+            warp_push(qt, q, qm, s_lo, E.lo);
+            warp_push(qt, q, qm, s_hi, E.hi);
+        }
+        if (!(ok = sync(PH_APPLY))) break;
+        const unsigned long long nrem_next = vload64(&C->spc[1]);
+        vq_t = vload64(&C->stail[0]);
+        eq_t = vload64(&C->stail[1]);
+
+        if (P.op == 0) {
+            // -------------------------------------------- DISCOVER (insert)
+            unsigned long long lo = vq0, hi = vq_t;
+            while (hi > lo) {
+                waves++;
+                FOR_EACH_VERTEX(C, P.VQ, qm, lo, hi, v)
+                    const int k = g.hs[v].x;
+                    const long long o = g.off[v];
+                    const int len = g.end[v];
+                    int pcd = 0;
+                    for (int t = lane; t < len; t += 32) {
+                        int w = g.adj[o + t];
+                        if (w >= 0) {
+                            int4 hw = g.hs[w];
+                            pcd += (hw.x > k) || (hw.x == k && hw.y > k);
+                        }
+                    }
+                    pcd = warp_sum(pcd);
+                    if (lane == 0) {
+                        g.hs[v].w = pcd;
+                        ls.vis++;
+                        ls.visl += len;
+                    }
+                    if (pcd > k) {
+                        for (int t0 = 0; t0 < len; t0 += 32) {
+                            int t = t0 + lane;
+                            int w = t < len ? g.adj[o + t] : HOLE;
+                            bool p = false;
+                            if (w >= 0) {
+                                int4 hw = g.hs[w];
+                                if (hw.x == k && hw.y > k && (uint32_t)hw.z != e)
+                                    p = atomicExch((unsigned int*)&g.hs[w].z, e) != e;
+                            }
+                            warp_push(&C->tail[0], P.VQ, qm, p, w);
+                        }
+                    } else {
+                        warp_push(&C->tail[1], P.EQ, qm, lane == 0, v);
+                    }
+                END_FOR_EACH_VERTEX
+                if (!(ok = sync(PH_DISCOVER))) break;
+                lo = hi;
+                hi = vload64(&C->stail[0]);
+            }
+            if (!ok) break;
+            vq_t = hi;
+            // -------------------------------------------- EVICT (insert)
+            lo = eq0;
+            hi = vload64(&C->stail[1]);
+            while (hi > lo) {
+                waves++;
+                FOR_EACH_VERTEX(C, P.EQ, qm, lo, hi, v)
+                    const int k = g.hs[v].x;
+                    const long long o = g.off[v];
+                    const int len = g.end[v];
+                    for (int t0 = 0; t0 < len; t0 += 32) {
+                        int t = t0 + lane;
+                        int w = t < len ? g.adj[o + t] : HOLE;
+                        bool p = false;
+                        if (w >= 0) {
+                            int4 hw = g.hs[w];
+                            if (hw.x == k && (uint32_t)hw.z == e && hw.w > k) p = atomicSub(&g.hs[w].w, 1) == k + 1;
+                        }
+                        warp_push(&C->tail[1], P.EQ, qm, p, w);
+                    }
+                    if (lane == 0) {
+                        ls.ev++;
+                        ls.evl += len;
+                    }
+                END_FOR_EACH_VERTEX
+                if (!(ok = sync(PH_EVICT))) break;
+                lo = hi;
+                hi = vload64(&C->stail[1]);
+            }
+            if (!ok) break;
+            eq_t = hi;
+            // -------------------------------------------- COMMIT (insert): survivors rise
+            for (long long base = gwarp * 32; base < (long long)(vq_t - vq0); base += nwarps * 32) {
+                long long i = base + lane;
+                bool up = false;
+                int v = 0;
+                if (i < (long long)(vq_t - vq0)) {
+                    v = P.VQ[(vq0 + i) & qm];
+                    int4 h = g.hs[v];
+                    if (h.w > h.x) {
+                        g.hs[v].x = h.x + 1;
+                        g.chg[v] = e;
+                        up = true;
+                    }
+                }
+                warp_push(&C->tail[2], P.CQ, qm, up, v);
+            }
+            if (!(ok = sync(PH_COMMIT))) break;
+            cq_t = vload64(&C->stail[2]);
+            fx = cq_t > cq0;
+            fx_lo = cq0;
+            fx_hi = cq_t;
+        } else {
+            // -------------------------------------------- EVICT (delete); evicted vertices drop by one
+            unsigned long long lo = eq0, hi = eq_t;
+            while (hi > lo) {
+                waves++;
+                FOR_EACH_VERTEX(C, P.EQ, qm, lo, hi, v)
+                    const int k = g.hs[v].x;
+                    const long long o = g.off[v];
+                    const int len = g.end[v];
+                    for (int t0 = 0; t0 < len; t0 += 32) {
+                        int t = t0 + lane;
+                        int w = t < len ? g.adj[o + t] : HOLE;
+                        bool p = false;
+                        if (w >= 0) {
+                            int4 hw = g.hs[w];
+                            // the live support of w is SD(w) minus its evicted neighbours so
+                            // far; w leaves when it first drops below k, i.e. when the count
+                            // reaches SD(w) - k + 1
+                            // reaches SD(w) - k + 1.  Evicted vertices (chg == e) are skipped:
+                            // their cores already dropped, so a vertex that fell from k+1
+                            // would otherwise pass for a level-k neighbour.
+                            const int thr = hw.y - k + 1;
+                            const bool gone = thr <= 0 || ((uint32_t)hw.z == e && hw.w >= thr);
+                            if (hw.x == k && !gone && g.chg[w] != e) {
+                                unsigned long long* pw = (unsigned long long*)&g.hs[w].z;
+                                unsigned long long old = vload64(pw);
+                                uint32_t cntw = 0;
+                                for (int tries = 0; tries < (1 << 22); tries++) {
+                                    uint32_t oe = (uint32_t)old, oc = (uint32_t)(old >> 32);
+                                    cntw = (oe == e) ? oc + 1 : 1;
+                                    unsigned long long nw = ((unsigned long long)cntw << 32) | e;
+                                    unsigned long long prev = atomicCAS(pw, old, nw);
+                                    if (prev == old) break;
+                                    old = prev;
+                                    cntw = 0;
+                                }
+                                if (cntw == 0) atomicCAS(&C->error, 0, E_ITER_LIMIT);
+                                p = (int)cntw == thr;
+                                if (p) g.chg[w] = e;
+                            }
+                        }
+                        warp_push(&C->tail[1], P.EQ, qm, p, w);
+                    }
+                    if (lane == 0) {
+                        g.hs[v].x = k - 1;
+                        ls.ev++;
+                        ls.evl += len;
+                    }
+                END_FOR_EACH_VERTEX
+                if (!(ok = sync(PH_EVICT))) break;
+                lo = hi;
+                hi = vload64(&C->stail[1]);
+            }
+            if (!ok) break;
+            eq_t = hi;
+            fx = eq_t > eq0;
+            fx_lo = eq0;
+            fx_hi = eq_t;
+        }
+        fx_e = e;
+        // ------------------------------------------------ next iteration, or hand over
+        const unsigned long long nsel = nrem - nrem_next;
+        const unsigned long long work = (vq_t - vq0) + (eq_t - eq0) + (cq_t - cq0) + nsel;
+        REdge* t = Rc;
+        Rc = Rn;
+        Rn = t;
+        nrem = nrem_next;
+        e++;
+        iters++;
+        if (nrem == 0) {
+            finished = 1;
+            break;
+        }
+        if (MODE == 0 && nrem <= (unsigned long long)P.small_edges && work <= (unsigned long long)P.small_work) {
+            next_want = 1;
+            break;
+        }
+        if (MODE == 1 && work > (unsigned long long)P.big_work) {
+            next_want = 0;
+            break;
+        }
+    }
+    if (ok && fx) {
+        fixup(g, C, P.op == 0 ? P.CQ : P.EQ, qm, fx_lo, fx_hi, fx_e, P.op, ls);
+        ok = sync(PH_FIXUP);
+    }
+    // statistics: one atomic per warp
+    if (lane == 0) {
+        if (ls.vis) atomicAdd(&C->st[ST_VISITED], (unsigned long long)ls.vis);
+        if (ls.visl) atomicAdd(&C->st[ST_VISSLOTS], (unsigned long long)ls.visl);
+        if (ls.ev) atomicAdd(&C->st[ST_EVICTED], (unsigned long long)ls.ev);
+        if (ls.evl) atomicAdd(&C->st[ST_EVSLOTS], (unsigned long long)ls.evl);
+        if (ls.ch) atomicAdd(&C->st[ST_CHANGED], (unsigned long long)ls.ch);
+        if (ls.chl) atomicAdd(&C->st[ST_CHSLOTS], (unsigned long long)ls.chl);
+    }
+    long long sel = ls.sel;
+    for (int o = 16; o > 0; o >>= 1) sel += __shfl_xor_sync(0xffffffffu, sel, o);
+    if (lane == 0 && sel) atomicAdd(&C->st[ST_SELECTED], (unsigned long long)sel);
+    if (leader) {
+        C->st[ST_ITERS] += (unsigned long long)iters;
+        if (MODE == 0) C->st[ST_GRID_ITERS] += (unsigned long long)iters;
+        C->st[ST_ROUNDS] += (unsigned long long)rounds;
+        C->st[ST_WAVES] += (unsigned long long)waves;
+        C->st[ST_REMSUM] += (unsigned long long)remsum;
+        if (ok) {
+            C->rs.nrem = nrem;
+            C->rs.rsel = Rc == P.R1 ? 1u : 0u;
+            C->rs.epoch = e;
+            C->rs.iters = iters0 + iters;
+            C->rs.done = finished;
+            C->rs.want = next_want;
+            __threadfence();
+        }
+    }
+}
+
+int maintain_blocks_per_sm(int threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, maintain_kernel<0>, threads, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_maintain(const MaintainParams& p, int blocks, int threads, cudaStream_t s) {
+    MaintainParams q = p;
+    void* args[] = {&q};
+    return cudaLaunchCooperativeKernel((const void*)maintain_kernel<0>, dim3(blocks), dim3(threads), args, 0, s);
+}
+
+cudaError_t launch_maintain_block(const MaintainParams& p, int threads, cudaStream_t s) {
+    maintain_kernel<1><<<1, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace cm

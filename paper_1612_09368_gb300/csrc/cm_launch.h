@@ -14,22 +14,24 @@ struct __align__(16) BSet {
     uint32_t pad;
 };
 
+// Parameters of a maintenance launch; where the call stands (remaining
+// edges, epoch, mode) lives in Ctl::rs.
 struct MaintainParams {
     DevGraph g;
     Ctl* ctl;
     REdge* R0;
     REdge* R1;
-    unsigned long long nrem0;
     int32_t* VQ;
     int32_t* EQ;
     int32_t* CQ;
     unsigned long long qmask;
-    uint32_t epoch0;
     int32_t op;               // 0 insert, 1 delete
     uint32_t expect;          // blocks a grid barrier waits for
-    uint32_t pad;
     unsigned long long limit_ns;
     long long max_iters;
+    long long small_edges;    // grid -> block mode when at most this many edges remain ...
+    long long small_work;     // ... and the last iteration touched at most this many items
+    long long big_work;       // block -> grid mode when an iteration touches more
 };
 
 struct PeelParams {
@@ -55,6 +57,7 @@ cudaError_t relocate(const int32_t* ovl, long long novl, DevGraph g, Ctl* c, cud
 cudaError_t clear_need(const REdge* R, long long n, DevGraph g, cudaStream_t s);
 cudaError_t apply_structure(const REdge* R, long long n, int op, DevGraph g, Ctl* c, cudaStream_t s);
 cudaError_t launch_maintain(const MaintainParams& p, int blocks, int threads, cudaStream_t s);
+cudaError_t launch_maintain_block(const MaintainParams& p, int threads, cudaStream_t s);
 int maintain_blocks_per_sm(int threads);
 
 // ---- store / peel (cm_store.cu)

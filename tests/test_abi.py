@@ -31,9 +31,10 @@ def test_library_exports_every_declared_entry_point(so):
 
 def test_binding_struct_layouts_match_header():
     import paper_1612_09368_gb300 as cm
-    # cm_options: 6 int32, int64, 3 pointers, 2 int32; cm_stats: 14 int64, 2 double, 8 int64
+    # cm_options: 6 int32, int64, 3 pointers, 2 int32
     assert ctypes.sizeof(cm.cm_options) == 6 * 4 + 8 + 3 * 8 + 2 * 4
-    assert ctypes.sizeof(cm.cm_stats) == 14 * 8 + 2 * 8 + 8 * 8
+    # cm_stats: 14 int64, 2 double, peel_levels, barriers, grid_iterations, phase_ns[7], reserved[4]
+    assert ctypes.sizeof(cm.cm_stats) == 14 * 8 + 2 * 8 + (3 + 7 + 4) * 8
 
 
 def test_default_options_without_gpu(so):
