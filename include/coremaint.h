@@ -224,6 +224,29 @@ int cm_multi_bases(const cm_graph* g, int32_t* bases, int32_t* ngraphs);
 int cm_update_multi(cm_graph* g, int32_t op, const int64_t* counts, const int32_t* edges,
                     int64_t* n_applied);
 
+/* ---------------- decomposition without device allocation ----------------
+ * The paper has no counterpart of this entry point; it serves callers that
+ * cannot call cudaMalloc -- a process whose framework already reserved the
+ * device memory for its own pool, or a latency-critical loop that must not
+ * wait on the allocator (cudaMalloc / cudaFree may synchronise the device).
+ *
+ * Computes the core number of every vertex of a static simple undirected
+ * graph given as CSR in DEVICE memory: row_off (n+1 int64, non-decreasing,
+ * row_off[0] = 0) and adj (row_off[n] int32 neighbour ids, every edge listed
+ * in both endpoints' rows).  cores (device, n int32) receives the result.
+ * Runs on `stream` (cudaStream_t) and returns after completion.  It
+ * allocates nothing: its scratch is one static device array sized for at
+ * most 1,048,576 vertices (16 MiB plus a 4 KiB control block), held by every
+ * GPU that loads the library until the process exits.  All calls share that
+ * array: calls whose work overlaps on the GPU (for example on two streams)
+ * race on it and must not be issued.  The first call on a device looks up
+ * the array's device address (once per device); make that first call
+ * before any stream capture.
+ * Errors: CM_ERR_INVALID (n < 0, NULL or host pointers), CM_ERR_CAPACITY
+ * (n > 1,048,576; nothing runs), CM_ERR_LIMIT (a bounded device wait ran
+ * out), CM_ERR_CUDA. */
+int cm_core_numbers_noalloc(int32_t n, const int64_t* row_off, const int32_t* adj, int32_t* cores, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
