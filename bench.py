@@ -253,6 +253,8 @@ def main():
     per_call_it = {k: [] for k in per_call_ms}
     per_call_grid_it = {k: 0 for k in per_call_ms}
     per_call_bar = {k: 0 for k in per_call_ms}
+    per_call_vol = {k: {"visited": 0, "visited_slots": 0, "evicted": 0, "evicted_slots": 0, "changed": 0,
+                        "changed_slots": 0, "waves": 0, "select_rounds": 0} for k in per_call_ms}
     phase_ns = {}
     for s in range(K):
         flush.fill_(s)
@@ -265,6 +267,8 @@ def main():
             per_call_it[name].append(x["iterations"])
             per_call_grid_it[name] += x["grid_iterations"]
             per_call_bar[name] += x["barriers"]
+            for vk in per_call_vol[name]:
+                per_call_vol[name][vk] += x[vk]
             for ph, ns in x["phase_ns"].items():
                 phase_ns[ph] = phase_ns.get(ph, 0) + ns
             maint_ms += x["maintain_ms"]
@@ -363,6 +367,7 @@ def main():
                            "call_ms_mean": {k: float(np.mean(v)) for k, v in per_call_ms.items()},
                            "iterations_mean": {k: float(np.mean(v)) for k, v in per_call_it.items()},
                            "grid_iterations": per_call_grid_it, "barriers": per_call_bar,
+                           "volumes": per_call_vol,
                            "phase_ms": {k: v / 1e6 for k, v in phase_ns.items()},
                            "maintain_ms_total": maint_ms, "units": units_all}}
         print(json.dumps(line), flush=True)

@@ -67,16 +67,18 @@ typedef void (*cm_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 typedef struct cm_options {
     int32_t slack_pct;      /* per-vertex adjacency headroom in percent (default 25) */
     int32_t min_cap;        /* minimum adjacency slots per vertex, rounded up to 4 (default 4) */
-    int32_t block_threads;  /* threads per block of the persistent kernels (default 512) */
+    int32_t block_threads;  /* threads per block of the peeling kernel (default 512) */
     int32_t blocks_per_sm;  /* resident blocks per SM of the persistent kernels; 0 = occupancy limit */
     int32_t max_sms;        /* SMs the persistent kernels may fill; 0 = all (lower it to share the GPU) */
-    int32_t reserved0;
+    int32_t block_mode_edges; /* single-block mode only while at most this many edges remain (16384) */
     int64_t spin_limit_ns;  /* limit of every grid-barrier wait (default 4e9 ns); CM_ERR_LIMIT past it */
     cm_alloc_fn alloc;      /* optional allocator, see above */
     cm_free_fn free;
     void* alloc_ctx;
     int32_t debug_flags;    /* test hooks, 0 in production (CM_DEBUG_*) */
-    int32_t reserved1;
+    int32_t block_mode_enter; /* grid -> single block after an iteration touching <= this many items (1024) */
+    int32_t block_mode_leave; /* single block -> grid after an iteration touching more (8192) */
+    int32_t reserved;
 } cm_options;
 
 /* Test hook: every grid barrier of the next maintenance launch waits for

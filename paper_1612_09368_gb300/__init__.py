@@ -47,9 +47,10 @@ _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_voi
 class cm_options(ctypes.Structure):
     _fields_ = [
         ("slack_pct", ctypes.c_int32), ("min_cap", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-        ("blocks_per_sm", ctypes.c_int32), ("max_sms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32), ("max_sms", ctypes.c_int32), ("block_mode_edges", ctypes.c_int32),
         ("spin_limit_ns", ctypes.c_int64), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p),
-        ("debug_flags", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("debug_flags", ctypes.c_int32), ("block_mode_enter", ctypes.c_int32), ("block_mode_leave", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

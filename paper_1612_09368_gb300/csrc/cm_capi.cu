@@ -62,7 +62,7 @@ struct cm_graph {
     cm_stats last{};
     long long launches = 0;
     // execution-mode thresholds of the maintenance kernel (see cm_iterate.cu)
-    long long small_edges = 1024, small_work = 2048, big_work = 16384;
+    long long small_edges = 16384, small_work = 1024, big_work = 8192;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -290,7 +290,7 @@ static int ensure_batch(cm_graph* h, long long k) {
 // as stay resident.  A small batch gets fewer blocks: grid barriers then
 // cost less, and there is not enough work for the whole GPU anyway.
 static void persistent_geometry(cm_graph* h, int kind, long long work, int* blocks, int* threads) {
-    int t = h->opt.block_threads > 0 ? h->opt.block_threads : 512;
+    int t = kind == 0 ? 512 : (h->opt.block_threads > 0 ? h->opt.block_threads : 512);   // maintenance blocks are 512 threads
     int occ = kind == 0 ? maintain_blocks_per_sm(t) : peel_blocks_per_sm(t);
     if (occ < 1) occ = 1;
     int bps = h->opt.blocks_per_sm > 0 ? (h->opt.blocks_per_sm < occ ? h->opt.blocks_per_sm : occ) : occ;
@@ -314,6 +314,9 @@ extern "C" void cm_default_options(cm_options* o) {
     o->min_cap = 4;
     o->block_threads = 512;
     o->spin_limit_ns = 4000000000ll;
+    o->block_mode_edges = 16384;
+    o->block_mode_enter = 1024;
+    o->block_mode_leave = 8192;
 }
 
 static void free_all(cm_graph* h) {
@@ -424,6 +427,9 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     if (h->opt.block_threads <= 0 || h->opt.block_threads > 512 || h->opt.block_threads % 32)
         h->opt.block_threads = 512;
     h->stream = (cudaStream_t)stream;
+    h->small_edges = h->opt.block_mode_edges > 0 ? h->opt.block_mode_edges : 16384;
+    h->small_work = h->opt.block_mode_enter > 0 ? h->opt.block_mode_enter : 1024;
+    h->big_work = h->opt.block_mode_leave > 0 ? h->opt.block_mode_leave : 8192;
     CK(h, cudaGetDevice(&h->device));
     CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     int coop = 0;
@@ -646,7 +652,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         rs.rsel = 0;
         rs.epoch = h->epoch;
         rs.done = 0;
-        rs.want = (!debug_hang && nrem0 <= h->small_edges) ? 1 : 0;
+        rs.want = (!debug_hang && nrem0 <= h->small_work) ? 1 : 0;
         rs.iters = 0;
         h->hctl->rs = rs;
         CK(h, cudaMemcpyAsync(&h->ctl->rs, &h->hctl->rs, sizeof(Resume), cudaMemcpyHostToDevice, h->stream));

@@ -44,13 +44,48 @@
 //            iteration's first claim phase and costs no barrier of its own.
 // All levels run together on the cores of the iteration's start: discovery
 // and eviction only ever follow neighbours of the vertex's own level.
+//
+// Per-vertex work of a wave is done by one warp per vertex (vertices fetched
+// dynamically); a vertex with at least kBigLen adjacency slots is deferred
+// and then processed by the whole block of the warp that fetched it.
 #include "cm_common.cuh"
 #include "cm_launch.h"
 
 namespace cm {
 
+constexpr int kBlockThreads = 1024;   // single-block mode
+constexpr int kGridThreads = 512;     // grid mode, per block
+constexpr int kBigLen = 256;
+constexpr int kMaxBig = 64;
+
 struct LocalStats {
     long long vis = 0, visl = 0, ev = 0, evl = 0, ch = 0, chl = 0, sel = 0;
+};
+
+// A group of threads sharing one vertex's adjacency: one warp, or the block.
+struct WarpGroup {
+    static constexpr int G = 32;
+    __device__ static int first() { return 0; }                    // first slot of this thread's warp
+    __device__ static bool rank0() { return lane_id() == 0; }
+    __device__ static bool warp0() { return true; }
+    __device__ static int sum(int v) { return warp_sum(v); }
+};
+template <int NT>
+struct BlockGroup {
+    static constexpr int G = NT;
+    __device__ static int first() { return threadIdx.x & ~31; }
+    __device__ static bool rank0() { return threadIdx.x == 0; }
+    __device__ static bool warp0() { return threadIdx.x < 32; }
+    __device__ static int sum(int v) {
+        __shared__ int s_part[NT / 32];
+        v = warp_sum(v);
+        __syncthreads();
+        if (lane_id() == 0) s_part[threadIdx.x >> 5] = v;
+        __syncthreads();
+        int t = 0;
+        for (int i = 0; i < NT / 32; i++) t += s_part[i];
+        return t;
+    }
 };
 
 template <int MODE>
@@ -71,6 +106,46 @@ struct Barrier {
         return ok;
     }
 };
+
+// Runs body(v, Group) for every vertex of ring[lo, hi): one warp per vertex
+// with dynamic fetching (pc[2]).  A vertex with at least kBigLen slots is
+// deferred by the warp that fetched it and then processed by that warp's
+// whole block (512 threads in grid mode, 1024 in single-block mode), so a
+// hub does not hold a wave on one warp.  Every thread of the launch must
+// call it.
+template <int MODE, class Body>
+__device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const int32_t* ring, unsigned long long qm,
+                                                unsigned long long lo, unsigned long long hi, Body body) {
+    constexpr int NT = MODE == 0 ? kGridThreads : kBlockThreads;
+    const int lane = lane_id();
+    __shared__ int s_big[kMaxBig];
+    __shared__ int s_nbig;
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
+    for (;;) {
+        unsigned long long j = 0;
+        if (lane == 0) j = atomicAdd(&C->pc[2], 1ull);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= hi - lo) break;
+        const int v = ring[(lo + j) & qm];
+        int defer = 0;
+        if (lane == 0 && g.end[v] >= kBigLen) {
+            int s = atomicAdd(&s_nbig, 1);
+            if (s < kMaxBig) {
+                s_big[s] = v;
+                defer = 1;
+            }
+        }
+        if (__shfl_sync(0xffffffffu, defer, 0)) continue;
+        body(v, WarpGroup{});
+    }
+    __syncthreads();
+    const int nb = min(s_nbig, kMaxBig);
+    for (int b = 0; b < nb; b++) {
+        body(s_big[b], BlockGroup<NT>{});
+        __syncthreads();
+    }
+}
 
 __device__ __forceinline__ void edge_level(const DevGraph& g, const REdge& E, int& k, bool& clo, bool& chi) {
     int a = g.hs[E.lo].x, b = g.hs[E.hi].x;
@@ -120,53 +195,154 @@ __device__ __forceinline__ int check_edge(const DevGraph& g, REdge* R, long long
     return 0;
 }
 
-// Warp-per-vertex loop over a ring range with dynamic fetching (pc[2]).
-#define FOR_EACH_VERTEX(C, ring, qm, lo, hi, v)                         \
-    for (;;) {                                                          \
-        unsigned long long j_ = 0;                                      \
-        if (lane == 0) j_ = atomicAdd(&(C)->pc[2], 1ull);               \
-        j_ = __shfl_sync(0xffffffffu, j_, 0);                           \
-        if (j_ >= (hi) - (lo)) break;                                   \
-        const int v = (ring)[((lo) + j_) & (qm)];
-
-#define END_FOR_EACH_VERTEX }
-
-// SD fix-up of the vertices whose core moved in iteration e.
-__device__ __forceinline__ void fixup(const DevGraph& g, Ctl* C, const int32_t* Q, unsigned long long qm,
-                                      unsigned long long lo, unsigned long long hi, uint32_t e, int op,
-                                      LocalStats& ls) {
+// ---------------------------------------------------------------- per-vertex phase bodies
+// Positive search step (Algorithm 3): CSD(v) becomes v's support; expand
+// to unvisited core-k neighbours with SD > k when CSD(v) > k, else v is
+// evicted at once.
+template <class Grp>
+__device__ __forceinline__ void discover_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                uint32_t e, LocalStats& ls) {
     const int lane = lane_id();
-    FOR_EACH_VERTEX(C, Q, qm, lo, hi, v)
-        const int kn = g.hs[v].x;
-        const long long o = g.off[v];
-        const int len = g.end[v];
-        const int adj_core = op == 0 ? kn : kn + 1;   // neighbours whose SD counts v differently now
-        int sd = 0;
-        for (int t = lane; t < len; t += 32) {
-            int w = g.adj[o + t];
+    const int k = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    int pcd = 0;
+    for (int t = Grp::first() + lane; t < len; t += Grp::G) {
+        int w = g.adj[o + t];
+        if (w >= 0) {
+            int4 hw = g.hs[w];
+            pcd += (hw.x > k) || (hw.x == k && hw.y > k);
+        }
+    }
+    pcd = Grp::sum(pcd);
+    if (Grp::rank0()) {
+        g.hs[v].w = pcd;
+        ls.vis++;
+        ls.visl += len;
+    }
+    if (pcd > k) {
+        for (int t0 = Grp::first(); t0 < len; t0 += Grp::G) {
+            int t = t0 + lane;
+            int w = t < len ? g.adj[o + t] : HOLE;
+            bool p = false;
             if (w >= 0) {
-                int cw = g.hs[w].x;
-                sd += cw >= kn;
-                if (cw == adj_core && g.chg[w] != e) {
-                    if (op == 0) atomicAdd(&g.hs[w].y, 1);
-                    else atomicSub(&g.hs[w].y, 1);
+                int4 hw = g.hs[w];
+                if (hw.x == k && hw.y > k && (uint32_t)hw.z != e) p = atomicExch((unsigned int*)&g.hs[w].z, e) != e;
+            }
+            warp_push(&C->tail[0], P.VQ, P.qmask, p, w);
+        }
+    } else if (Grp::warp0()) {
+        warp_push(&C->tail[1], P.EQ, P.qmask, lane == 0, v);
+    }
+}
+
+// InsertRemove step (Algorithm 4): v leaves; each visited core-k neighbour
+// loses one support and leaves when its support falls to k.
+template <class Grp>
+__device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                    uint32_t e, LocalStats& ls) {
+    const int lane = lane_id();
+    const int k = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    for (int t0 = Grp::first(); t0 < len; t0 += Grp::G) {
+        int t = t0 + lane;
+        int w = t < len ? g.adj[o + t] : HOLE;
+        bool p = false;
+        if (w >= 0) {
+            int4 hw = g.hs[w];
+            if (hw.x == k && (uint32_t)hw.z == e && hw.w > k) p = atomicSub(&g.hs[w].w, 1) == k + 1;
+        }
+        warp_push(&C->tail[1], P.EQ, P.qmask, p, w);
+    }
+    if (Grp::rank0()) {
+        ls.ev++;
+        ls.evl += len;
+    }
+}
+
+// DeleteRemove step (Algorithm 7): v drops to k-1; each core-k neighbour w
+// loses one support (initially SD(w)) and leaves when it falls below k,
+// i.e. when its count of evicted neighbours reaches SD(w) - k + 1.
+template <class Grp>
+__device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                    uint32_t e, LocalStats& ls) {
+    const int lane = lane_id();
+    const int k = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    for (int t0 = Grp::first(); t0 < len; t0 += Grp::G) {
+        int t = t0 + lane;
+        int w = t < len ? g.adj[o + t] : HOLE;
+        bool p = false;
+        if (w >= 0) {
+            int4 hw = g.hs[w];
+            const int thr = hw.y - k + 1;
+            const bool gone = thr <= 0 || ((uint32_t)hw.z == e && hw.w >= thr);
+            // evicted vertices (chg == e) are skipped: their cores already
+            // dropped, so one that fell from k+1 would pass for level k
+            if (hw.x == k && !gone && g.chg[w] != e) {
+                unsigned long long* pw = (unsigned long long*)&g.hs[w].z;
+                unsigned long long old = vload64(pw);
+                uint32_t cntw = 0;
+                for (int tries = 0; tries < (1 << 22); tries++) {
+                    uint32_t oe = (uint32_t)old, oc = (uint32_t)(old >> 32);
+                    cntw = (oe == e) ? oc + 1 : 1;
+                    unsigned long long nw = ((unsigned long long)cntw << 32) | e;
+                    unsigned long long prev = atomicCAS(pw, old, nw);
+                    if (prev == old) break;
+                    old = prev;
+                    cntw = 0;
                 }
+                if (cntw == 0) atomicCAS(&C->error, 0, E_ITER_LIMIT);
+                p = (int)cntw == thr;
+                if (p) g.chg[w] = e;
             }
         }
-        sd = warp_sum(sd);
-        if (lane == 0) {
-            g.hs[v].y = sd;
-            ls.ch++;
-            ls.chl += len;
+        warp_push(&C->tail[1], P.EQ, P.qmask, p, w);
+    }
+    if constexpr (Grp::G > 32) __syncthreads();   // every warp has read k before it changes
+    if (Grp::rank0()) {
+        g.hs[v].x = k - 1;
+        ls.ev++;
+        ls.evl += len;
+    }
+}
+
+// SD fix-up of a vertex whose core moved in iteration e (op 0 rose, op 1 dropped).
+template <class Grp>
+__device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t e, int op, LocalStats& ls) {
+    const int lane = lane_id();
+    const int kn = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    const int adj_core = op == 0 ? kn : kn + 1;   // neighbours whose SD counts v differently now
+    int sd = 0;
+    for (int t = Grp::first() + lane; t < len; t += Grp::G) {
+        int w = g.adj[o + t];
+        if (w >= 0) {
+            int cw = g.hs[w].x;
+            sd += cw >= kn;
+            if (cw == adj_core && g.chg[w] != e) {
+                if (op == 0) atomicAdd(&g.hs[w].y, 1);
+                else atomicSub(&g.hs[w].y, 1);
+            }
         }
-    END_FOR_EACH_VERTEX
+    }
+    sd = Grp::sum(sd);
+    if (Grp::rank0()) {
+        g.hs[v].y = sd;
+        ls.ch++;
+        ls.chl += len;
+    }
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(MODE == 0 ? 512 : 1024, MODE == 0 ? 2 : 1) maintain_kernel(MaintainParams P) {
+__global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE == 0 ? 2 : 1)
+    maintain_kernel(MaintainParams P) {
     Ctl* C = P.ctl;
     const DevGraph g = P.g;
-    // where to resume (host or the other mode wrote it before this launch)
+    // where to resume (the host or the other mode wrote it before this launch)
     const int done0 = *(volatile int*)&C->rs.done;
     const int want = *(volatile int*)&C->rs.want;
     if (done0 || want != MODE || vload32(&C->error)) return;
@@ -191,6 +367,8 @@ __global__ void __launch_bounds__(MODE == 0 ? 512 : 1024, MODE == 0 ? 2 : 1) mai
     unsigned long long fx_lo = 0, fx_hi = 0;
     uint32_t fx_e = 0;
     int next_want = MODE, finished = 0;
+    const int32_t* FXQ = P.op == 0 ? P.CQ : P.EQ;
+    auto fixup_body = [&](int v, auto grp) { fixup_vertex<decltype(grp)>(g, v, fx_e, P.op, ls); };
 
     while (nrem > 0) {
         if (iters0 + iters >= P.max_iters) {
@@ -203,7 +381,7 @@ __global__ void __launch_bounds__(MODE == 0 ? 512 : 1024, MODE == 0 ? 2 : 1) mai
         int r = 0;
         for (;;) {
             if (r == 0 && fx) {
-                fixup(g, C, P.op == 0 ? P.CQ : P.EQ, qm, fx_lo, fx_hi, fx_e, P.op, ls);
+                for_each_vertex<MODE>(g, C, FXQ, qm, fx_lo, fx_hi, fixup_body);
                 fx = false;
             }
             for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
@@ -301,40 +479,9 @@ __global__ void __launch_bounds__(MODE == 0 ? 512 : 1024, MODE == 0 ? 2 : 1) mai
             unsigned long long lo = vq0, hi = vq_t;
             while (hi > lo) {
                 waves++;
-                FOR_EACH_VERTEX(C, P.VQ, qm, lo, hi, v)
-                    const int k = g.hs[v].x;
-                    const long long o = g.off[v];
-                    const int len = g.end[v];
-                    int pcd = 0;
-                    for (int t = lane; t < len; t += 32) {
-                        int w = g.adj[o + t];
-                        if (w >= 0) {
-                            int4 hw = g.hs[w];
-                            pcd += (hw.x > k) || (hw.x == k && hw.y > k);
-                        }
-                    }
-                    pcd = warp_sum(pcd);
-                    if (lane == 0) {
-                        g.hs[v].w = pcd;
-                        ls.vis++;
-                        ls.visl += len;
-                    }
-                    if (pcd > k) {
-                        for (int t0 = 0; t0 < len; t0 += 32) {
-                            int t = t0 + lane;
-                            int w = t < len ? g.adj[o + t] : HOLE;
-                            bool p = false;
-                            if (w >= 0) {
-                                int4 hw = g.hs[w];
-                                if (hw.x == k && hw.y > k && (uint32_t)hw.z != e)
-                                    p = atomicExch((unsigned int*)&g.hs[w].z, e) != e;
-                            }
-                            warp_push(&C->tail[0], P.VQ, qm, p, w);
-                        }
-                    } else {
-                        warp_push(&C->tail[1], P.EQ, qm, lane == 0, v);
-                    }
-                END_FOR_EACH_VERTEX
+                for_each_vertex<MODE>(g, C, P.VQ, qm, lo, hi, [&](int v, auto grp) {
+                    discover_vertex<decltype(grp)>(g, C, P, v, e, ls);
+                });
                 if (!(ok = sync(PH_DISCOVER))) break;
                 lo = hi;
                 hi = vload64(&C->stail[0]);
@@ -346,25 +493,9 @@ __global__ void __launch_bounds__(MODE == 0 ? 512 : 1024, MODE == 0 ? 2 : 1) mai
             hi = vload64(&C->stail[1]);
             while (hi > lo) {
                 waves++;
-                FOR_EACH_VERTEX(C, P.EQ, qm, lo, hi, v)
-                    const int k = g.hs[v].x;
-                    const long long o = g.off[v];
-                    const int len = g.end[v];
-                    for (int t0 = 0; t0 < len; t0 += 32) {
-                        int t = t0 + lane;
-                        int w = t < len ? g.adj[o + t] : HOLE;
-                        bool p = false;
-                        if (w >= 0) {
-                            int4 hw = g.hs[w];
-                            if (hw.x == k && (uint32_t)hw.z == e && hw.w > k) p = atomicSub(&g.hs[w].w, 1) == k + 1;
-                        }
-                        warp_push(&C->tail[1], P.EQ, qm, p, w);
-                    }
-                    if (lane == 0) {
-                        ls.ev++;
-                        ls.evl += len;
-                    }
-                END_FOR_EACH_VERTEX
+                for_each_vertex<MODE>(g, C, P.EQ, qm, lo, hi, [&](int v, auto grp) {
+                    evict_insert_vertex<decltype(grp)>(g, C, P, v, e, ls);
+                });
                 if (!(ok = sync(PH_EVICT))) break;
                 lo = hi;
                 hi = vload64(&C->stail[1]);
@@ -397,50 +528,9 @@ __global__ void __launch_bounds__(MODE == 0 ? 512 : 1024, MODE == 0 ? 2 : 1) mai
             unsigned long long lo = eq0, hi = eq_t;
             while (hi > lo) {
                 waves++;
-                FOR_EACH_VERTEX(C, P.EQ, qm, lo, hi, v)
-                    const int k = g.hs[v].x;
-                    const long long o = g.off[v];
-                    const int len = g.end[v];
-                    for (int t0 = 0; t0 < len; t0 += 32) {
-                        int t = t0 + lane;
-                        int w = t < len ? g.adj[o + t] : HOLE;
-                        bool p = false;
-                        if (w >= 0) {
-                            int4 hw = g.hs[w];
-                            // the live support of w is SD(w) minus its evicted neighbours so
-                            // far; w leaves when it first drops below k, i.e. when the count
-                            // reaches SD(w) - k + 1
-                            // reaches SD(w) - k + 1.  Evicted vertices (chg == e) are skipped:
-                            // their cores already dropped, so a vertex that fell from k+1
-                            // would otherwise pass for a level-k neighbour.
-                            const int thr = hw.y - k + 1;
-                            const bool gone = thr <= 0 || ((uint32_t)hw.z == e && hw.w >= thr);
-                            if (hw.x == k && !gone && g.chg[w] != e) {
-                                unsigned long long* pw = (unsigned long long*)&g.hs[w].z;
-                                unsigned long long old = vload64(pw);
-                                uint32_t cntw = 0;
-                                for (int tries = 0; tries < (1 << 22); tries++) {
-                                    uint32_t oe = (uint32_t)old, oc = (uint32_t)(old >> 32);
-                                    cntw = (oe == e) ? oc + 1 : 1;
-                                    unsigned long long nw = ((unsigned long long)cntw << 32) | e;
-                                    unsigned long long prev = atomicCAS(pw, old, nw);
-                                    if (prev == old) break;
-                                    old = prev;
-                                    cntw = 0;
-                                }
-                                if (cntw == 0) atomicCAS(&C->error, 0, E_ITER_LIMIT);
-                                p = (int)cntw == thr;
-                                if (p) g.chg[w] = e;
-                            }
-                        }
-                        warp_push(&C->tail[1], P.EQ, qm, p, w);
-                    }
-                    if (lane == 0) {
-                        g.hs[v].x = k - 1;
-                        ls.ev++;
-                        ls.evl += len;
-                    }
-                END_FOR_EACH_VERTEX
+                for_each_vertex<MODE>(g, C, P.EQ, qm, lo, hi, [&](int v, auto grp) {
+                    evict_delete_vertex<decltype(grp)>(g, C, P, v, e, ls);
+                });
                 if (!(ok = sync(PH_EVICT))) break;
                 lo = hi;
                 hi = vload64(&C->stail[1]);
@@ -475,7 +565,7 @@ __global__ void __launch_bounds__(MODE == 0 ? 512 : 1024, MODE == 0 ? 2 : 1) mai
         }
     }
     if (ok && fx) {
-        fixup(g, C, P.op == 0 ? P.CQ : P.EQ, qm, fx_lo, fx_hi, fx_e, P.op, ls);
+        for_each_vertex<MODE>(g, C, FXQ, qm, fx_lo, fx_hi, fixup_body);
         ok = sync(PH_FIXUP);
     }
     // statistics: one atomic per warp
@@ -521,7 +611,8 @@ cudaError_t launch_maintain(const MaintainParams& p, int blocks, int threads, cu
 }
 
 cudaError_t launch_maintain_block(const MaintainParams& p, int threads, cudaStream_t s) {
-    maintain_kernel<1><<<1, threads, 0, s>>>(p);
+    (void)threads;
+    maintain_kernel<1><<<1, kBlockThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
