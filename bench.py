@@ -55,7 +55,7 @@ def kernel_traffic():
     try:
         with open(os.path.join(ROOT, "profiles", "maintain_traffic.json")) as f:
             t = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1612_09368_gb300", "csrc", "cm_maintain.cu"), "rb").read()
+        src = open(os.path.join(ROOT, "paper_1612_09368_gb300", "csrc", "cm_iterate.cu"), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != t.get("source_sha"):
             return None
         return t.get("dram_bytes_per_launch")
