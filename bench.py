@@ -192,19 +192,105 @@ def run_round(g, r, dev_inputs, cm):
     return a + b + c + d, st
 
 
+def run_sweep(args):
+    """R-MAT scale-24 batch sweep (the HBM-roofline workload): per operation,
+    batch size and endpoint law, the maintenance call and the full re-peel
+    comparator (structure update + GPU peeling), each undone untimed so
+    every case starts from the same graph."""
+    import torch
+    import paper_1612_09368_gb300 as cm
+    from paper_1612_09368_gb300 import build as libbuild
+    from synth import workloads
+
+    libbuild.build()
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    t0 = time.time()
+    n, e, batches = workloads.rmat_sweep(scale=args.scale, sizes=sizes)
+    gen_s = time.time() - t0
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = cm.CoreGraph(n, torch.from_numpy(e).to(dev), stream=stream)
+    create = g.stats()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    peak, peak_kind = load_peaks()
+    cases = []
+    clk = ClockSampler(0)
+    clk.start()
+    for (op, size, law), b in sorted(batches.items(), key=lambda x: (x[0][1], x[0][0], x[0][2])):
+        db = torch.from_numpy(b).to(dev)
+        fwd = g.insert_edges if op == "insert" else g.delete_edges
+        inv = g.delete_edges if op == "insert" else g.insert_edges
+        rec = {"op": op, "batch": size, "law": "uniform" if law == 0 else "degree-proportional"}
+        ms, st = [], None
+        for rep in range(args.reps):
+            flush.fill_(rep)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            applied = fwd(db)
+            a1.record(stream)
+            a1.synchronize()
+            ms.append(a0.elapsed_time(a1))
+            st = g.stats()
+            inv(db)
+        flush.fill_(7)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        g.apply_edges(cm.CM_OP_INSERT if op == "insert" else cm.CM_OP_DELETE, db)
+        g.recompute_cores()
+        r1.record(stream)
+        r1.synchronize()
+        rp = r0.elapsed_time(r1)
+        levels = g.stats()["peel_levels"]
+        g.apply_edges(cm.CM_OP_DELETE if op == "insert" else cm.CM_OP_INSERT, db)
+        g.recompute_cores()
+        call_ms = statistics.median(ms)
+        achieved = st["alg_bytes"] / (st["maintain_ms"] / 1000.0) / 1e9 if st["maintain_ms"] else 0.0
+        rec.update({"applied": applied, "call_ms": call_ms, "edge_updates_per_s": applied / (call_ms / 1000.0),
+                    "iterations": st["iterations"], "grid_iterations": st["grid_iterations"],
+                    "waves": st["waves"], "barriers": st["barriers"],
+                    "maintain_ms": st["maintain_ms"], "alg_bytes": st["alg_bytes"], "achieved_gbs": achieved,
+                    "frac": achieved / peak, "visited": st["visited"], "visited_slots": st["visited_slots"],
+                    "evicted": st["evicted"], "evicted_slots": st["evicted_slots"], "changed": st["changed"],
+                    "repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": levels})
+        cases.append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+    clocks = clk.stop()
+    best = max(cases, key=lambda c: c["frac"])
+    line = {"metric": METRIC, "workload": f"rmat{args.scale}-sweep", "unit": UNIT, "n_gpus": 1,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}-sweep", "scale": args.scale, "edge_factor": 16,
+                       "vertices": n, "edges": int(len(e)), "batch_sizes": list(sizes),
+                       "laws": ["uniform", "degree-proportional"], "reps": args.reps,
+                       "l2": "flushed before every timed call (256 MiB write)"},
+            "peak": peak, "peak_kind": peak_kind, "clocks": clocks, "generation_s": gen_s,
+            "create_ms": create["call_ms"], "create_peel_levels": create["peel_levels"],
+            "best_roofline_case": {k: best[k] for k in ("op", "batch", "law", "achieved_gbs", "frac")},
+            "sweep": cases}
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--workload", default="rmat20-rounds", choices=["rmat20-rounds", "rmat24-sweep"])
+    ap.add_argument("--scale", type=int, default=None)
+    ap.add_argument("--sizes", default="1000,10000,100000,1000000")
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
+    if args.scale is None:
+        args.scale = 24 if args.workload == "rmat24-sweep" else 20
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "rmat24-sweep":
+        return run_sweep(args)
 
     import torch
     import paper_1612_09368_gb300 as cm

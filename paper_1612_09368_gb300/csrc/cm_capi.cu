@@ -615,7 +615,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
             return set_err(h, CM_ERR_LIMIT, "structure update failed with device error %d", c.error);
         }
     } else if (nrem0 > 0) {
-        if (h->epoch > 0xF0000000u) {   // stamps about to wrap: clear them
+        if (h->epoch > 0x3F000000u) {   // 30-bit stamps about to wrap: clear them
             CK(h, cudaMemsetAsync(g.chg, 0, (size_t)h->n * 4, h->stream));
             CK(h, cudaMemsetAsync(g.taken, 0, (size_t)h->n * 4, h->stream));
             CK(h, cudaMemset2DAsync((char*)g.hs + 8, sizeof(int4), 0, 8, (size_t)h->n, h->stream));
@@ -652,7 +652,9 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         rs.rsel = 0;
         rs.epoch = h->epoch;
         rs.done = 0;
-        rs.want = (!debug_hang && nrem0 <= h->small_work) ? 1 : 0;
+        // every call starts grid-wide: even one edge can start a search over a
+        // whole dense shell; the kernel hands down after a small iteration
+        rs.want = 0;
         rs.iters = 0;
         h->hctl->rs = rs;
         CK(h, cudaMemcpyAsync(&h->ctl->rs, &h->hctl->rs, sizeof(Resume), cudaMemcpyHostToDevice, h->stream));

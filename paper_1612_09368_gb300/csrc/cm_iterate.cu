@@ -3,7 +3,7 @@
 // maintain_kernel<MODE> runs the iterations of SuperiorEdgeInsert
 // (Algorithm 1) or SuperiorEdgeDelete (Algorithm 5) on the remaining edges
 // of a batch.  MODE 0 is a cooperative launch filling the GPU, with grid-wide
-// barriers; MODE 1 is one block of 1024 threads with __syncthreads barriers,
+// barriers; MODE 1 is one block of 512 threads with __syncthreads barriers,
 // for the long tail of iterations that carry little work (a barrier there
 // costs ~0.1 us instead of a few us).  Either kernel stops at an iteration
 // boundary when the other mode suits the work better and records where to
@@ -22,16 +22,20 @@
 //            (lexicographically first) maximal set in priority order.
 //   APPLY    insert / delete the selected edges in the slack CSR and move
 //            SD (superior degree, Definition 7) of constrained endpoints.
-//   insert:  DISCOVER the candidate sets of all levels at once -- the exKPT
-//            of Definition 10, walked breadth-first from the constrained
-//            endpoints through vertices w with core(w) = k and SD(w) > k,
-//            expanding only from vertices whose CSD (Definition 8) exceeds
-//            k (the positive search of Algorithm 3).  A vertex's support
-//            starts at its CSD.  EVICT in waves: a vertex whose support is
-//            <= k cannot rise (Lemma 8); it takes one support from every
-//            visited core-k neighbour, which leaves when its support falls to
-//            k (InsertRemove, Algorithm 4).  COMMIT: survivors rise by one
-//            (Algorithm 1 line 7, Lemma 7).
+//   insert:  positive and negative search of Algorithms 3-4, run as
+//            breadth-first waves in which both progress together.  The
+//            constrained endpoints are the first frontier.  Processing a
+//            frontier vertex v adds CSD(v) (Definition 8) to its support
+//            count, which already holds one decrement per evicted neighbour
+//            (the paper's pre-decremented cd).  If the count exceeds k, v
+//            visits its unvisited core-k neighbours with SD > k (the next
+//            frontier); otherwise v is evicted (Lemma 8).  An evicted vertex
+//            takes one from the count of every core-k neighbour with SD > k,
+//            visited or not; a processed neighbour whose count falls to k is
+//            evicted too (InsertRemove, Algorithm 4).  Frontier and evictions
+//            of a wave run in the same phase, so evictions prune the search
+//            as it grows.  COMMIT: processed vertices still above k rise by
+//            one (Algorithm 1 line 7, Lemma 7).
 //   delete:  EVICT in waves from the constrained endpoints whose SD fell
 //            below k (Algorithm 6); an evicted vertex drops by one and takes
 //            one from the support (initially SD) of every core-k neighbour,
@@ -42,51 +46,24 @@
 //            (insert) or old core (delete).  It only writes SD, which the
 //            next iteration first reads in APPLY, so it runs inside the next
 //            iteration's first claim phase and costs no barrier of its own.
-// All levels run together on the cores of the iteration's start: discovery
-// and eviction only ever follow neighbours of the vertex's own level.
+// All levels run together on the cores of the iteration's start: searches
+// and evictions only ever follow neighbours of the vertex's own level.
+//
+// The per-vertex bodies and the per-iteration vertex word are in cm_vertex.cuh.
 //
 // Per-vertex work of a wave is done by one warp per vertex (vertices fetched
 // dynamically); a vertex with at least kBigLen adjacency slots is deferred
 // and then processed by the whole block of the warp that fetched it.
 #include "cm_common.cuh"
 #include "cm_launch.h"
+#include "cm_vertex.cuh"
 
 namespace cm {
 
-constexpr int kBlockThreads = 1024;   // single-block mode
+constexpr int kBlockThreads = 512;    // single-block mode
 constexpr int kGridThreads = 512;     // grid mode, per block
 constexpr int kBigLen = 256;
 constexpr int kMaxBig = 64;
-
-struct LocalStats {
-    long long vis = 0, visl = 0, ev = 0, evl = 0, ch = 0, chl = 0, sel = 0;
-};
-
-// A group of threads sharing one vertex's adjacency: one warp, or the block.
-struct WarpGroup {
-    static constexpr int G = 32;
-    __device__ static int first() { return 0; }                    // first slot of this thread's warp
-    __device__ static bool rank0() { return lane_id() == 0; }
-    __device__ static bool warp0() { return true; }
-    __device__ static int sum(int v) { return warp_sum(v); }
-};
-template <int NT>
-struct BlockGroup {
-    static constexpr int G = NT;
-    __device__ static int first() { return threadIdx.x & ~31; }
-    __device__ static bool rank0() { return threadIdx.x == 0; }
-    __device__ static bool warp0() { return threadIdx.x < 32; }
-    __device__ static int sum(int v) {
-        __shared__ int s_part[NT / 32];
-        v = warp_sum(v);
-        __syncthreads();
-        if (lane_id() == 0) s_part[threadIdx.x >> 5] = v;
-        __syncthreads();
-        int t = 0;
-        for (int i = 0; i < NT / 32; i++) t += s_part[i];
-        return t;
-    }
-};
 
 template <int MODE>
 struct Barrier {
@@ -108,14 +85,15 @@ struct Barrier {
 };
 
 // Runs body(v, Group) for every vertex of ring[lo, hi): one warp per vertex
-// with dynamic fetching (pc[2]).  A vertex with at least kBigLen slots is
-// deferred by the warp that fetched it and then processed by that warp's
-// whole block (512 threads in grid mode, 1024 in single-block mode), so a
-// hub does not hold a wave on one warp.  Every thread of the launch must
-// call it.
+// with dynamic fetching (counter *ctr, zeroed at every barrier).  A vertex
+// with at least kBigLen slots is deferred by the warp that fetched it and
+// then processed by that warp's whole block (512 threads in either mode,
+// in single-block mode), so a hub does not hold a wave on one warp.  Every
+// thread of the launch must call it.
 template <int MODE, class Body>
-__device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const int32_t* ring, unsigned long long qm,
-                                                unsigned long long lo, unsigned long long hi, Body body) {
+__device__ __forceinline__ void for_each_vertex(const DevGraph& g, unsigned long long* ctr, const int32_t* ring,
+                                                unsigned long long qm, unsigned long long lo, unsigned long long hi,
+                                                Body body) {
     constexpr int NT = MODE == 0 ? kGridThreads : kBlockThreads;
     const int lane = lane_id();
     __shared__ int s_big[kMaxBig];
@@ -124,7 +102,7 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
     __syncthreads();
     for (;;) {
         unsigned long long j = 0;
-        if (lane == 0) j = atomicAdd(&C->pc[2], 1ull);
+        if (lane == 0) j = atomicAdd(ctr, 1ull);
         j = __shfl_sync(0xffffffffu, j, 0);
         if (j >= hi - lo) break;
         const int v = ring[(lo + j) & qm];
@@ -195,148 +173,6 @@ __device__ __forceinline__ int check_edge(const DevGraph& g, REdge* R, long long
     return 0;
 }
 
-// ---------------------------------------------------------------- per-vertex phase bodies
-// Positive search step (Algorithm 3): CSD(v) becomes v's support; expand
-// to unvisited core-k neighbours with SD > k when CSD(v) > k, else v is
-// evicted at once.
-template <class Grp>
-__device__ __forceinline__ void discover_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                uint32_t e, LocalStats& ls) {
-    const int lane = lane_id();
-    const int k = g.hs[v].x;
-    const long long o = g.off[v];
-    const int len = g.end[v];
-    int pcd = 0;
-    for (int t = Grp::first() + lane; t < len; t += Grp::G) {
-        int w = g.adj[o + t];
-        if (w >= 0) {
-            int4 hw = g.hs[w];
-            pcd += (hw.x > k) || (hw.x == k && hw.y > k);
-        }
-    }
-    pcd = Grp::sum(pcd);
-    if (Grp::rank0()) {
-        g.hs[v].w = pcd;
-        ls.vis++;
-        ls.visl += len;
-    }
-    if (pcd > k) {
-        for (int t0 = Grp::first(); t0 < len; t0 += Grp::G) {
-            int t = t0 + lane;
-            int w = t < len ? g.adj[o + t] : HOLE;
-            bool p = false;
-            if (w >= 0) {
-                int4 hw = g.hs[w];
-                if (hw.x == k && hw.y > k && (uint32_t)hw.z != e) p = atomicExch((unsigned int*)&g.hs[w].z, e) != e;
-            }
-            warp_push(&C->tail[0], P.VQ, P.qmask, p, w);
-        }
-    } else if (Grp::warp0()) {
-        warp_push(&C->tail[1], P.EQ, P.qmask, lane == 0, v);
-    }
-}
-
-// InsertRemove step (Algorithm 4): v leaves; each visited core-k neighbour
-// loses one support and leaves when its support falls to k.
-template <class Grp>
-__device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                    uint32_t e, LocalStats& ls) {
-    const int lane = lane_id();
-    const int k = g.hs[v].x;
-    const long long o = g.off[v];
-    const int len = g.end[v];
-    for (int t0 = Grp::first(); t0 < len; t0 += Grp::G) {
-        int t = t0 + lane;
-        int w = t < len ? g.adj[o + t] : HOLE;
-        bool p = false;
-        if (w >= 0) {
-            int4 hw = g.hs[w];
-            if (hw.x == k && (uint32_t)hw.z == e && hw.w > k) p = atomicSub(&g.hs[w].w, 1) == k + 1;
-        }
-        warp_push(&C->tail[1], P.EQ, P.qmask, p, w);
-    }
-    if (Grp::rank0()) {
-        ls.ev++;
-        ls.evl += len;
-    }
-}
-
-// DeleteRemove step (Algorithm 7): v drops to k-1; each core-k neighbour w
-// loses one support (initially SD(w)) and leaves when it falls below k,
-// i.e. when its count of evicted neighbours reaches SD(w) - k + 1.
-template <class Grp>
-__device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                    uint32_t e, LocalStats& ls) {
-    const int lane = lane_id();
-    const int k = g.hs[v].x;
-    const long long o = g.off[v];
-    const int len = g.end[v];
-    for (int t0 = Grp::first(); t0 < len; t0 += Grp::G) {
-        int t = t0 + lane;
-        int w = t < len ? g.adj[o + t] : HOLE;
-        bool p = false;
-        if (w >= 0) {
-            int4 hw = g.hs[w];
-            const int thr = hw.y - k + 1;
-            const bool gone = thr <= 0 || ((uint32_t)hw.z == e && hw.w >= thr);
-            // evicted vertices (chg == e) are skipped: their cores already
-            // dropped, so one that fell from k+1 would pass for level k
-            if (hw.x == k && !gone && g.chg[w] != e) {
-                unsigned long long* pw = (unsigned long long*)&g.hs[w].z;
-                unsigned long long old = vload64(pw);
-                uint32_t cntw = 0;
-                for (int tries = 0; tries < (1 << 22); tries++) {
-                    uint32_t oe = (uint32_t)old, oc = (uint32_t)(old >> 32);
-                    cntw = (oe == e) ? oc + 1 : 1;
-                    unsigned long long nw = ((unsigned long long)cntw << 32) | e;
-                    unsigned long long prev = atomicCAS(pw, old, nw);
-                    if (prev == old) break;
-                    old = prev;
-                    cntw = 0;
-                }
-                if (cntw == 0) atomicCAS(&C->error, 0, E_ITER_LIMIT);
-                p = (int)cntw == thr;
-                if (p) g.chg[w] = e;
-            }
-        }
-        warp_push(&C->tail[1], P.EQ, P.qmask, p, w);
-    }
-    if constexpr (Grp::G > 32) __syncthreads();   // every warp has read k before it changes
-    if (Grp::rank0()) {
-        g.hs[v].x = k - 1;
-        ls.ev++;
-        ls.evl += len;
-    }
-}
-
-// SD fix-up of a vertex whose core moved in iteration e (op 0 rose, op 1 dropped).
-template <class Grp>
-__device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t e, int op, LocalStats& ls) {
-    const int lane = lane_id();
-    const int kn = g.hs[v].x;
-    const long long o = g.off[v];
-    const int len = g.end[v];
-    const int adj_core = op == 0 ? kn : kn + 1;   // neighbours whose SD counts v differently now
-    int sd = 0;
-    for (int t = Grp::first() + lane; t < len; t += Grp::G) {
-        int w = g.adj[o + t];
-        if (w >= 0) {
-            int cw = g.hs[w].x;
-            sd += cw >= kn;
-            if (cw == adj_core && g.chg[w] != e) {
-                if (op == 0) atomicAdd(&g.hs[w].y, 1);
-                else atomicSub(&g.hs[w].y, 1);
-            }
-        }
-    }
-    sd = Grp::sum(sd);
-    if (Grp::rank0()) {
-        g.hs[v].y = sd;
-        ls.ch++;
-        ls.chl += len;
-    }
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE == 0 ? 2 : 1)
     maintain_kernel(MaintainParams P) {
@@ -381,7 +217,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         int r = 0;
         for (;;) {
             if (r == 0 && fx) {
-                for_each_vertex<MODE>(g, C, FXQ, qm, fx_lo, fx_hi, fixup_body);
+                for_each_vertex<MODE>(g, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
                 fx = false;
             }
             for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
@@ -432,14 +268,9 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                         }
                         atomicAdd(&g.deg[E.lo], 1);
                         atomicAdd(&g.deg[E.hi], 1);
-                        if (clo) {
-                            int m = atomicAdd(&g.hs[E.lo].y, 1) + 1;
-                            s_lo = m > k && atomicExch((unsigned int*)&g.hs[E.lo].z, e) != e;
-                        }
-                        if (chi) {
-                            int m = atomicAdd(&g.hs[E.hi].y, 1) + 1;
-                            s_hi = m > k && atomicExch((unsigned int*)&g.hs[E.hi].z, e) != e;
-                        }
+                        // a constrained endpoint's SD rises; with SD > k it roots the search
+                        if (clo) s_lo = atomicAdd(&g.hs[E.lo].y, 1) + 1 > k && visit(g, C, E.lo, e);
+                        if (chi) s_hi = atomicAdd(&g.hs[E.hi].y, 1) + 1 > k && visit(g, C, E.hi, e);
                     } else {
                         Bucket b = g.idx[E.bkt];
                         if (b.slo >= 0 && b.slo < g.end[E.lo] && b.shi >= 0 && b.shi < g.end[E.hi]) {
@@ -475,33 +306,25 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         eq_t = vload64(&C->stail[1]);
 
         if (P.op == 0) {
-            // -------------------------------------------- DISCOVER (insert)
-            unsigned long long lo = vq0, hi = vq_t;
-            while (hi > lo) {
+            // -------------------------------------------- SEARCH (insert): frontier + evictions per wave
+            unsigned long long flo = vq0, fhi = vq_t, elo = eq0, ehi = eq_t;
+            while (fhi > flo || ehi > elo) {
                 waves++;
-                for_each_vertex<MODE>(g, C, P.VQ, qm, lo, hi, [&](int v, auto grp) {
-                    discover_vertex<decltype(grp)>(g, C, P, v, e, ls);
+                for_each_vertex<MODE>(g, &C->pc[2], P.VQ, qm, flo, fhi, [&](int v, auto grp) {
+                    process_frontier<decltype(grp)>(g, C, P, v, e, ls);
                 });
-                if (!(ok = sync(PH_DISCOVER))) break;
-                lo = hi;
-                hi = vload64(&C->stail[0]);
-            }
-            if (!ok) break;
-            vq_t = hi;
-            // -------------------------------------------- EVICT (insert)
-            lo = eq0;
-            hi = vload64(&C->stail[1]);
-            while (hi > lo) {
-                waves++;
-                for_each_vertex<MODE>(g, C, P.EQ, qm, lo, hi, [&](int v, auto grp) {
+                for_each_vertex<MODE>(g, &C->pc[3], P.EQ, qm, elo, ehi, [&](int v, auto grp) {
                     evict_insert_vertex<decltype(grp)>(g, C, P, v, e, ls);
                 });
-                if (!(ok = sync(PH_EVICT))) break;
-                lo = hi;
-                hi = vload64(&C->stail[1]);
+                if (!(ok = sync(PH_DISCOVER))) break;
+                flo = fhi;
+                fhi = vload64(&C->stail[0]);
+                elo = ehi;
+                ehi = vload64(&C->stail[1]);
             }
             if (!ok) break;
-            eq_t = hi;
+            vq_t = fhi;
+            eq_t = ehi;
             // -------------------------------------------- COMMIT (insert): survivors rise
             for (long long base = gwarp * 32; base < (long long)(vq_t - vq0); base += nwarps * 32) {
                 long long i = base + lane;
@@ -528,7 +351,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             unsigned long long lo = eq0, hi = eq_t;
             while (hi > lo) {
                 waves++;
-                for_each_vertex<MODE>(g, C, P.EQ, qm, lo, hi, [&](int v, auto grp) {
+                for_each_vertex<MODE>(g, &C->pc[2], P.EQ, qm, lo, hi, [&](int v, auto grp) {
                     evict_delete_vertex<decltype(grp)>(g, C, P, v, e, ls);
                 });
                 if (!(ok = sync(PH_EVICT))) break;
@@ -565,7 +388,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         }
     }
     if (ok && fx) {
-        for_each_vertex<MODE>(g, C, FXQ, qm, fx_lo, fx_hi, fixup_body);
+        for_each_vertex<MODE>(g, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
         ok = sync(PH_FIXUP);
     }
     // statistics: one atomic per warp

@@ -1,0 +1,280 @@
+// cm_vertex.cuh -- per-vertex work of the maintenance waves (included by
+// cm_iterate.cu only).
+//
+// Each body scans one vertex's adjacency with a group of threads: one warp,
+// or a whole block for a high-degree vertex.  Scans read the list four slots
+// per thread with one 16-byte load (lists start 16-byte aligned and their
+// capacity is a multiple of 4, so the load never leaves the list's
+// allocation) and issue the four neighbour gathers before using any, so a
+// warp keeps four independent loads in flight per lane.  Loops are
+// warp-uniform, so warp collectives may run inside them.
+//
+// The per-iteration word of a vertex is hs.z / hs.w, read and updated as one
+// 64-bit value: z = stamp (iteration << 2 | flags), w = a count.  A word
+// with an older stamp reads as "no flags, count 0"; the first update in an
+// iteration stamps it with one CAS, later updates are single atomicAdd /
+// atomicOr operations on the 64-bit word.  Insert flags: 1 visited (in a
+// frontier), 2 processed (CSD added); w = support.  Delete: w = evicted
+// neighbours.
+#pragma once
+#include "cm_common.cuh"
+#include "cm_launch.h"
+
+namespace cm {
+
+constexpr uint32_t kVisited = 1u, kProcessed = 2u;
+
+struct LocalStats {
+    long long vis = 0, visl = 0, ev = 0, evl = 0, ch = 0, chl = 0, sel = 0;
+};
+
+// ---------------------------------------------------------------- per-iteration word
+__device__ __forceinline__ bool same_iter(uint32_t z, uint32_t e) { return (z >> 2) == e; }
+__device__ __forceinline__ unsigned long long* iter_word(const DevGraph& g, int v) {
+    return reinterpret_cast<unsigned long long*>(&g.hs[v].z);
+}
+__device__ __forceinline__ uint32_t wz(unsigned long long x) { return (uint32_t)x; }
+__device__ __forceinline__ int32_t ww(unsigned long long x) { return (int32_t)(uint32_t)(x >> 32); }
+
+// Stamps v's word with iteration e if it is older (count 0, no flags).
+// Retries are bounded; past the bound an error is recorded.
+__device__ __forceinline__ void make_current(const DevGraph& g, Ctl* C, int v, uint32_t e) {
+    unsigned long long* p = iter_word(g, v);
+    unsigned long long old = vload64(p);
+    const unsigned long long fresh = (unsigned long long)(e << 2);
+    for (int tries = 0; tries < (1 << 20); tries++) {
+        if (same_iter(wz(old), e)) return;
+        unsigned long long prev = atomicCAS(p, old, fresh);
+        if (prev == old) return;
+        old = prev;
+    }
+    atomicCAS(&C->error, 0, E_ITER_LIMIT);
+}
+
+// Adds delta to v's count and low_add to its flag bits (only bits that are
+// clear); returns the previous (flags, count) of iteration e.
+__device__ __forceinline__ void add_word(const DevGraph& g, Ctl* C, int v, uint32_t e, int32_t delta,
+                                         uint32_t low_add, uint32_t& oflags, int32_t& ocount) {
+    make_current(g, C, v, e);
+    unsigned long long old =
+        atomicAdd(iter_word(g, v), ((unsigned long long)(uint32_t)delta << 32) + (unsigned long long)low_add);
+    oflags = wz(old) & 3u;
+    ocount = ww(old);
+}
+
+// Marks v visited in iteration e; true if this call did it.
+__device__ __forceinline__ bool visit(const DevGraph& g, Ctl* C, int v, uint32_t e) {
+    make_current(g, C, v, e);
+    unsigned long long old = atomicOr(iter_word(g, v), (unsigned long long)kVisited);
+    return (wz(old) & kVisited) == 0;
+}
+
+// ---------------------------------------------------------------- thread groups
+// A group of threads sharing one vertex's adjacency: one warp, or the block.
+struct WarpGroup {
+    static constexpr int G = 32;
+    __device__ static int first() { return 0; }                    // first thread of this warp in the group
+    __device__ static bool rank0() { return lane_id() == 0; }
+    __device__ static bool warp0() { return true; }
+    __device__ static int sum(int v) { return warp_sum(v); }
+};
+template <int NT>
+struct BlockGroup {
+    static constexpr int G = NT;
+    __device__ static int first() { return threadIdx.x & ~31; }
+    __device__ static bool rank0() { return threadIdx.x == 0; }
+    __device__ static bool warp0() { return threadIdx.x < 32; }
+    __device__ static int sum(int v) {
+        __shared__ int s_part[NT / 32];
+        v = warp_sum(v);
+        __syncthreads();
+        if (lane_id() == 0) s_part[threadIdx.x >> 5] = v;
+        __syncthreads();
+        int t = 0;
+        for (int i = 0; i < NT / 32; i++) t += s_part[i];
+        return t;
+    }
+};
+
+// Four neighbour ids of this lane for the step starting at `base` (HOLE for
+// slots at or past len).
+__device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, int t0, int w[4]) {
+    int4 a = make_int4(HOLE, HOLE, HOLE, HOLE);
+    if (t0 < len) a = *reinterpret_cast<const int4*>(g.adj + o + t0);
+    w[0] = a.x;
+    w[1] = t0 + 1 < len ? a.y : HOLE;
+    w[2] = t0 + 2 < len ? a.z : HOLE;
+    w[3] = t0 + 3 < len ? a.w : HOLE;
+}
+
+#define SCAN4_BEGIN(Grp, len)                                                   \
+    for (int base_ = Grp::first() * 4; base_ < (len); base_ += Grp::G * 4) {     \
+        const int t0_ = base_ + lane_id() * 4;
+#define SCAN4_END }
+
+// ---------------------------------------------------------------- per-vertex phase bodies
+// Positive search step (Algorithm 3) for a frontier vertex v at level k:
+// support += CSD(v); above k -> visit the unvisited core-k neighbours with
+// SD > k, else v is evicted.
+template <class Grp>
+__device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                 uint32_t e, LocalStats& ls) {
+    const int lane = lane_id();
+    const int k = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    int pcd = 0;
+    SCAN4_BEGIN(Grp, len)
+        int w[4];
+        load4(g, o, len, t0_, w);
+        int2 h[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? *reinterpret_cast<const int2*>(&g.hs[w[q]]) : make_int2(-1, 0);
+#pragma unroll
+        for (int q = 0; q < 4; q++) pcd += (h[q].x > k) || (h[q].x == k && h[q].y > k);
+    SCAN4_END
+    pcd = Grp::sum(pcd);
+    int32_t sup = 0;
+    if (Grp::rank0()) {
+        uint32_t of;
+        int32_t oc;
+        add_word(g, C, v, e, pcd, kProcessed, of, oc);
+        sup = oc + pcd;
+        ls.vis++;
+        ls.visl += len;
+    }
+    if constexpr (Grp::G == 32) {
+        sup = __shfl_sync(0xffffffffu, sup, 0);
+    } else {
+        sup = Grp::sum(Grp::rank0() ? sup : 0);
+    }
+    if (sup > k) {
+        SCAN4_BEGIN(Grp, len)
+            int w[4];
+            load4(g, o, len, t0_, w);
+            int4 h[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
+                bool p = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e);
+                warp_push(&C->tail[0], P.VQ, P.qmask, p, w[q]);
+            }
+        SCAN4_END
+    } else if (Grp::warp0()) {
+        warp_push(&C->tail[1], P.EQ, P.qmask, lane == 0, v);
+    }
+}
+
+// InsertRemove step (Algorithm 4): v leaves; every core-k neighbour with
+// SD > k (visited or not) loses one support; a processed one whose support
+// falls to k leaves too.
+template <class Grp>
+__device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                    uint32_t e, LocalStats& ls) {
+    const int k = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    SCAN4_BEGIN(Grp, len)
+        int w[4];
+        load4(g, o, len, t0_, w);
+        int4 h[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const bool gone = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kProcessed) && h[q].w <= k;
+            bool p = false;
+            if (h[q].x == k && h[q].y > k && !gone) {
+                uint32_t of;
+                int32_t oc;
+                add_word(g, C, w[q], e, -1, 0u, of, oc);
+                p = (of & kProcessed) && oc == k + 1;
+            }
+            warp_push(&C->tail[1], P.EQ, P.qmask, p, w[q]);
+        }
+    SCAN4_END
+    if (Grp::rank0()) {
+        ls.ev++;
+        ls.evl += len;
+    }
+}
+
+// DeleteRemove step (Algorithm 7): v drops to k-1; each core-k neighbour w
+// loses one support (initially SD(w)) and leaves when it falls below k,
+// i.e. when its count of evicted neighbours reaches SD(w) - k + 1.
+template <class Grp>
+__device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                    uint32_t e, LocalStats& ls) {
+    const int k = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    SCAN4_BEGIN(Grp, len)
+        int w[4];
+        load4(g, o, len, t0_, w);
+        int4 h[4];
+        uint32_t c[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+            c[q] = w[q] >= 0 ? g.chg[w[q]] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int thr = h[q].y - k + 1;
+            const bool gone = thr <= 0 || (same_iter((uint32_t)h[q].z, e) && h[q].w >= thr);
+            bool p = false;
+            // evicted vertices (chg == e) are skipped: their cores already
+            // dropped, so one that fell from k+1 would pass for level k
+            if (h[q].x == k && !gone && c[q] != e) {
+                uint32_t of;
+                int32_t oc;
+                add_word(g, C, w[q], e, 1, 0u, of, oc);
+                p = oc + 1 == thr;
+                if (p) g.chg[w[q]] = e;
+            }
+            warp_push(&C->tail[1], P.EQ, P.qmask, p, w[q]);
+        }
+    SCAN4_END
+    if constexpr (Grp::G > 32) __syncthreads();   // every warp has read k before it changes
+    if (Grp::rank0()) {
+        g.hs[v].x = k - 1;
+        ls.ev++;
+        ls.evl += len;
+    }
+}
+
+// SD fix-up of a vertex whose core moved in iteration e (op 0 rose, op 1 dropped).
+template <class Grp>
+__device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t e, int op, LocalStats& ls) {
+    const int kn = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    const int adj_core = op == 0 ? kn : kn + 1;   // neighbours whose SD counts v differently now
+    int sd = 0;
+    SCAN4_BEGIN(Grp, len)
+        int w[4];
+        load4(g, o, len, t0_, w);
+        int cw[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) cw[q] = w[q] >= 0 ? g.hs[w[q]].x : -1;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (w[q] < 0) continue;
+            sd += cw[q] >= kn;
+            if (cw[q] == adj_core && g.chg[w[q]] != e) {
+                if (op == 0) atomicAdd(&g.hs[w[q]].y, 1);
+                else atomicSub(&g.hs[w[q]].y, 1);
+            }
+        }
+    SCAN4_END
+    sd = Grp::sum(sd);
+    if (Grp::rank0()) {
+        g.hs[v].y = sd;
+        ls.ch++;
+        ls.chl += len;
+    }
+}
+
+}  // namespace cm

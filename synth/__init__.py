@@ -71,6 +71,9 @@ def _L():
                 "sy_dyn_add_vertices": (i64, [vp, i32, i32, u64, _i32p]),
                 "sy_dyn_delete_vertices": (i64, [vp, i32, u64, _i32p]),
                 "sy_dyn_incident": (i64, [vp, i32, _i32p]),
+                "sy_static_sample_insert": (i64, [_i32p, i64, i32, i64, i32, u64, _i32p]),
+                "sy_static_sample_delete": (i64, [_i32p, i64, i32, _i64p, _i32p, i64, i32, u64, _i32p]),
+                "sy_csr": (ctypes.c_int, [i32, i64, _i32p, _i64p, _i32p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -137,6 +140,38 @@ def grid(side: int, nshort: int, seed: int) -> np.ndarray:
     if got != cnt:
         raise ValueError(f"sy_grid failed ({got})")
     return out
+
+
+def csr(n: int, edges: np.ndarray):
+    """(row_off int64[n+1], adj int32[2m]) listing every edge in both rows."""
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    row_off = np.empty(n + 1, dtype=np.int64)
+    adj = np.empty(2 * len(e), dtype=np.int32)
+    if _L().sy_csr(n, len(e), _p32(e), row_off.ctypes.data_as(_i64p), _p32(adj)) != 0:
+        raise MemoryError("sy_csr")
+    return row_off, adj
+
+
+def static_sample_insert(n: int, edges: np.ndarray, count: int, law: int, seed: int) -> np.ndarray:
+    """New edges for a large static graph (no dynamic model needed)."""
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    out = np.empty((count, 2), dtype=np.int32)
+    got = _L().sy_static_sample_insert(_p32(e), len(e), n, count, law, seed, _p32(out))
+    if got < 0:
+        raise MemoryError("sy_static_sample_insert")
+    return out[:got].copy()
+
+
+def static_sample_delete(n: int, edges: np.ndarray, count: int, law: int, seed: int, csr_=None) -> np.ndarray:
+    """Existing edges of a large static graph; law UNIFORM needs csr_ = csr(n, edges)."""
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    out = np.empty((count, 2), dtype=np.int32)
+    ro, ad = (None, None) if csr_ is None else csr_
+    got = _L().sy_static_sample_delete(_p32(e), len(e), n, None if ro is None else ro.ctypes.data_as(_i64p),
+                                       None if ad is None else _p32(ad), count, law, seed, _p32(out))
+    if got < 0:
+        raise MemoryError("sy_static_sample_delete")
+    return out[:got].copy()
 
 
 class DynGraph:

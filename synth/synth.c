@@ -497,3 +497,97 @@ int64_t sy_dyn_incident(const sy_dyn* d, int32_t v, int32_t* out) {
     for (int32_t i = 0; i < d->deg[v]; i++) { out[2 * i] = v; out[2 * i + 1] = d->adj[v][i].w; }
     return d->deg[v];
 }
+
+/* ---------------- batch samplers for a large static graph ----------------
+ * For graphs too large for the dynamic model: `keys` are the graph's
+ * canonical edge keys (lo << 32 | hi) sorted increasingly (sy_rmat's output
+ * order), `edges` the same edges as pairs. */
+static int key_present(const uint64_t* keys, int64_t m, uint64_t k) {
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return lo < m && keys[lo] == k;
+}
+
+/* New edges (absent from the graph, distinct, u != v).  law 0: endpoints
+ * uniform in [0, n); law 1: endpoints degree-proportional (an endpoint of a
+ * uniform edge). */
+int64_t sy_static_sample_insert(const int32_t* edges, int64_t m, int32_t n, int64_t count, int32_t law,
+                                uint64_t seed, int32_t* out) {
+    uint64_t* keys = (uint64_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(uint64_t));
+    if (!keys) return -2;
+    for (int64_t i = 0; i < m; i++) keys[i] = ekey(edges[2 * i], edges[2 * i + 1]);
+    int sorted = 1;
+    for (int64_t i = 1; i < m && sorted; i++) if (keys[i] <= keys[i - 1]) sorted = 0;
+    if (!sorted && radix_sort_u64(keys, m)) { free(keys); return -2; }
+    hmap b; if (hm_init(&b, count)) { free(keys); return -2; }
+    rng_t r = {seed, 0};
+    int64_t got = 0, tries = 0, lim = 64 * count + 1024;
+    while (got < count && tries < lim) {
+        tries++;
+        int32_t u, v;
+        if (law == 1 && m > 0) {
+            uint64_t x = rnext(&r), y = rnext(&r);
+            int64_t e1 = (int64_t)below(x, (uint64_t)m), e2 = (int64_t)below(y, (uint64_t)m);
+            u = (x & 1) ? edges[2 * e1] : edges[2 * e1 + 1];
+            v = (y & 1) ? edges[2 * e2] : edges[2 * e2 + 1];
+        } else {
+            u = (int32_t)below(rnext(&r), (uint64_t)n);
+            v = (int32_t)below(rnext(&r), (uint64_t)n);
+        }
+        if (u == v) continue;
+        uint64_t k = ekey(u, v);
+        if (key_present(keys, m, k)) continue;
+        if (hm_put(&b, k, got)) { out[2 * got] = u; out[2 * got + 1] = v; got++; }
+    }
+    hm_free(&b);
+    free(keys);
+    return got;
+}
+
+/* Existing edges (distinct).  law 1: a uniform random edge (endpoints
+ * degree-proportional); law 0: a uniform vertex with degree > 0, then a
+ * uniform neighbour of it (needs the CSR row_off/adj of the graph). */
+int64_t sy_static_sample_delete(const int32_t* edges, int64_t m, int32_t n, const int64_t* row_off,
+                                const int32_t* adj, int64_t count, int32_t law, uint64_t seed, int32_t* out) {
+    if (count > m) count = m;
+    hmap b; if (hm_init(&b, count)) return -2;
+    rng_t r = {seed, 0};
+    int64_t got = 0, tries = 0, lim = 64 * count + 1024;
+    while (got < count && tries < lim) {
+        tries++;
+        int32_t u, v;
+        if (law == 1 || !row_off) {
+            int64_t e = (int64_t)below(rnext(&r), (uint64_t)m);
+            u = edges[2 * e]; v = edges[2 * e + 1];
+        } else {
+            u = (int32_t)below(rnext(&r), (uint64_t)n);
+            int64_t d = row_off[u + 1] - row_off[u];
+            if (d == 0) continue;
+            v = adj[row_off[u] + (int64_t)below(rnext(&r), (uint64_t)d)];
+        }
+        uint64_t k = ekey(u, v);
+        if (hm_put(&b, k, got)) { out[2 * got] = u; out[2 * got + 1] = v; got++; }
+    }
+    hm_free(&b);
+    return got;
+}
+
+/* CSR (both directions) of an edge list: row_off has n+1 entries, adj 2m. */
+int sy_csr(int32_t n, int64_t m, const int32_t* edges, int64_t* row_off, int32_t* adj) {
+    memset(row_off, 0, (size_t)(n + 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < m; i++) { row_off[edges[2 * i] + 1]++; row_off[edges[2 * i + 1] + 1]++; }
+    for (int32_t v = 0; v < n; v++) row_off[v + 1] += row_off[v];
+    int64_t* fill = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!fill) return -2;
+    memcpy(fill, row_off, (size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < m; i++) {
+        int32_t u = edges[2 * i], v = edges[2 * i + 1];
+        adj[fill[u]++] = v;
+        adj[fill[v]++] = u;
+    }
+    free(fill);
+    return 0;
+}

@@ -85,19 +85,24 @@ def rmat_rounds(rounds: int, scale: int = 20, edge_factor: int = 16, ins: int = 
     return w
 
 
-def rmat_sweep(scale: int = 24, edge_factor: int = 16, sizes=(10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6), cfg: int = 3):
-    """R-MAT graph plus, per batch size and law (uniform / degree-proportional
-    endpoints), an insert batch of new edges and a delete batch of existing
-    edges, each drawn against the original graph."""
+def rmat_sweep(scale: int = 24, edge_factor: int = 16, sizes=(10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6), cfg: int = 3,
+               ops=("insert", "delete"), laws=(UNIFORM, PREFERENTIAL)):
+    """R-MAT graph plus, per batch size and endpoint law (uniform /
+    degree-proportional), an insert batch of new edges and a delete batch of
+    existing edges, each drawn against the original graph."""
+    from . import csr, static_sample_delete, static_sample_insert
     e = rmat(scale, edge_factor, stream(cfg, 0, 0, GRAPH))
     n = 1 << scale
-    d = DynGraph(n, e)
+    c = csr(n, e) if ("delete" in ops and UNIFORM in laws) else None
     batches = {}
     for i, s in enumerate(sizes):
-        for law in (UNIFORM, PREFERENTIAL):
-            batches[("insert", s, law)] = d.sample_insert(s, law, stream(cfg, 0, 2 * i + law, INSERT))
-            batches[("delete", s, law)] = d.sample_delete(s, law, stream(cfg, 0, 2 * i + law, DELETE))
-    return n, e, batches, d
+        for law in laws:
+            if "insert" in ops:
+                batches[("insert", s, law)] = static_sample_insert(n, e, s, law, stream(cfg, 0, 2 * i + law, INSERT))
+            if "delete" in ops:
+                batches[("delete", s, law)] = static_sample_delete(n, e, s, law, stream(cfg, 0, 2 * i + law, DELETE),
+                                                                   c)
+    return n, e, batches
 
 
 def ba_many(ngraphs: int = 512, cfg: int = 4, nmin_exp: float = 3.0, nmax_exp: float = 6.0):
