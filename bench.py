@@ -205,7 +205,8 @@ def run_sweep(args):
     libbuild.build()
     sizes = tuple(int(x) for x in args.sizes.split(","))
     t0 = time.time()
-    n, e, batches = workloads.rmat_sweep(scale=args.scale, sizes=sizes)
+    ops = tuple(args.ops.split(","))
+    n, e, batches = workloads.rmat_sweep(scale=args.scale, sizes=sizes, ops=ops)
     gen_s = time.time() - t0
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
@@ -281,6 +282,7 @@ def main():
     ap.add_argument("--scale", type=int, default=None)
     ap.add_argument("--sizes", default="1000,10000,100000,1000000")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--ops", default="insert,delete")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

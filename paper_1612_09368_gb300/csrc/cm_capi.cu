@@ -637,6 +637,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         p.small_edges = h->small_edges;
         p.small_work = h->small_work;
         p.big_work = h->big_work;
+        p.big_wave = h->big_work / 8 > 64 ? h->big_work / 8 : 64;
         int blocks, threads;
         persistent_geometry(h, 0, nrem0, &blocks, &threads);
         p.expect = (uint32_t)blocks;

@@ -60,13 +60,17 @@ enum { PH_CLAIM = 0, PH_CHECK, PH_APPLY, PH_DISCOVER, PH_EVICT, PH_COMMIT, PH_FI
 // launch of a call and by a kernel that hands the call over to the other
 // execution mode (grid-wide or single-block) at an iteration boundary.
 struct Resume {
-    unsigned long long nrem;   // remaining edges
+    unsigned long long nrem;   // remaining edges (mid: those left for the next iteration)
     uint32_t rsel;             // which remaining-edge buffer holds them
-    uint32_t epoch;            // next iteration's stamp
+    uint32_t epoch;            // next iteration's stamp (mid: the current one)
     int done;                  // every edge applied
     int want;                  // 0: grid mode next, 1: single-block mode next
-    long long iters;           // iterations so far (for the cap)
-    long long pad;
+    long long iters;           // completed iterations (for the cap)
+    int mid;                   // 1: resume inside the search waves of iteration `epoch`
+    int pad;
+    // mid-search state: ring positions at the iteration's start and the
+    // pending frontier / eviction ranges of the next wave
+    unsigned long long vq0, eq0, cq0, flo, fhi, elo, ehi;
 };
 
 // Device control block, one per handle.  The barrier words and counters are

@@ -197,6 +197,23 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     unsigned long long vq_t = vload64(&C->tail[0]), eq_t = vload64(&C->tail[1]), cq_t = vload64(&C->tail[2]);
     LocalStats ls;
     long long iters = 0, rounds = 0, waves = 0, remsum = 0;
+    // resume inside the search waves of an iteration the single-block mode began
+    bool mid = *(volatile int*)&C->rs.mid != 0;
+    bool escalate = false;
+    unsigned long long nrem_next = 0, vq0 = 0, eq0 = 0, cq0 = 0, flo = 0, fhi = 0, elo = 0, ehi = 0;
+    if (mid) {
+        nrem_next = nrem;                  // edges left for the next iteration, in buffer rsel
+        REdge* t0 = Rc;
+        Rc = Rn;
+        Rn = t0;
+        vq0 = vload64(&C->rs.vq0);
+        eq0 = vload64(&C->rs.eq0);
+        cq0 = vload64(&C->rs.cq0);
+        flo = vload64(&C->rs.flo);
+        fhi = vload64(&C->rs.fhi);
+        elo = vload64(&C->rs.elo);
+        ehi = vload64(&C->rs.ehi);
+    }
     bool ok = true;
     // pending SD fix-up of the previous iteration
     bool fx = false;
@@ -206,7 +223,8 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     const int32_t* FXQ = P.op == 0 ? P.CQ : P.EQ;
     auto fixup_body = [&](int v, auto grp) { fixup_vertex<decltype(grp)>(g, v, fx_e, P.op, ls); };
 
-    while (nrem > 0) {
+    while (mid || nrem > 0) {
+      if (!mid) {
         if (iters0 + iters >= P.max_iters) {
             if (leader) atomicCAS(&C->error, 0, E_ITER_LIMIT);
             ok = false;
@@ -239,7 +257,9 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         if (!ok) break;
         rounds += r;
         // ------------------------------------------------ APPLY
-        const unsigned long long vq0 = vq_t, eq0 = eq_t, cq0 = cq_t;
+        vq0 = vq_t;
+        eq0 = eq_t;
+        cq0 = cq_t;
         for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
             long long i = base + lane;
             bool valid = i < (long long)nrem;
@@ -301,14 +321,23 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             warp_push(qt, q, qm, s_hi, E.hi);
         }
         if (!(ok = sync(PH_APPLY))) break;
-        const unsigned long long nrem_next = vload64(&C->spc[1]);
+        nrem_next = vload64(&C->spc[1]);
         vq_t = vload64(&C->stail[0]);
         eq_t = vload64(&C->stail[1]);
+        flo = vq0;
+        fhi = vq_t;
+        elo = eq0;
+        ehi = eq_t;
+      }
+      mid = false;
 
         if (P.op == 0) {
             // -------------------------------------------- SEARCH (insert): frontier + evictions per wave
-            unsigned long long flo = vq0, fhi = vq_t, elo = eq0, ehi = eq_t;
             while (fhi > flo || ehi > elo) {
+                if (MODE == 1 && (fhi - flo) + (ehi - elo) > (unsigned long long)P.big_wave) {
+                    escalate = true;   // this wave is too big for one block: hand it to the grid
+                    break;
+                }
                 waves++;
                 for_each_vertex<MODE>(g, &C->pc[2], P.VQ, qm, flo, fhi, [&](int v, auto grp) {
                     process_frontier<decltype(grp)>(g, C, P, v, e, ls);
@@ -322,7 +351,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                 elo = ehi;
                 ehi = vload64(&C->stail[1]);
             }
-            if (!ok) break;
+            if (!ok || escalate) break;
             vq_t = fhi;
             eq_t = ehi;
             // -------------------------------------------- COMMIT (insert): survivors rise
@@ -348,18 +377,21 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             fx_hi = cq_t;
         } else {
             // -------------------------------------------- EVICT (delete); evicted vertices drop by one
-            unsigned long long lo = eq0, hi = eq_t;
-            while (hi > lo) {
+            while (ehi > elo) {
+                if (MODE == 1 && ehi - elo > (unsigned long long)P.big_wave) {
+                    escalate = true;
+                    break;
+                }
                 waves++;
-                for_each_vertex<MODE>(g, &C->pc[2], P.EQ, qm, lo, hi, [&](int v, auto grp) {
+                for_each_vertex<MODE>(g, &C->pc[2], P.EQ, qm, elo, ehi, [&](int v, auto grp) {
                     evict_delete_vertex<decltype(grp)>(g, C, P, v, e, ls);
                 });
                 if (!(ok = sync(PH_EVICT))) break;
-                lo = hi;
-                hi = vload64(&C->stail[1]);
+                elo = ehi;
+                ehi = vload64(&C->stail[1]);
             }
-            if (!ok) break;
-            eq_t = hi;
+            if (!ok || escalate) break;
+            eq_t = ehi;
             fx = eq_t > eq0;
             fx_lo = eq0;
             fx_hi = eq_t;
@@ -409,13 +441,30 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         C->st[ST_ROUNDS] += (unsigned long long)rounds;
         C->st[ST_WAVES] += (unsigned long long)waves;
         C->st[ST_REMSUM] += (unsigned long long)remsum;
-        if (ok) {
+        if (ok && escalate) {
+            C->rs.nrem = nrem_next;
+            C->rs.rsel = Rn == P.R1 ? 1u : 0u;
+            C->rs.epoch = e;
+            C->rs.iters = iters0 + iters;
+            C->rs.done = 0;
+            C->rs.want = 0;
+            C->rs.mid = 1;
+            C->rs.vq0 = vq0;
+            C->rs.eq0 = eq0;
+            C->rs.cq0 = cq0;
+            C->rs.flo = flo;
+            C->rs.fhi = fhi;
+            C->rs.elo = elo;
+            C->rs.ehi = ehi;
+            __threadfence();
+        } else if (ok) {
             C->rs.nrem = nrem;
             C->rs.rsel = Rc == P.R1 ? 1u : 0u;
             C->rs.epoch = e;
             C->rs.iters = iters0 + iters;
             C->rs.done = finished;
             C->rs.want = next_want;
+            C->rs.mid = 0;
             __threadfence();
         }
     }

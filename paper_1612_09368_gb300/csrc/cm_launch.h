@@ -32,6 +32,7 @@ struct MaintainParams {
     long long small_edges;    // grid -> block mode when at most this many edges remain ...
     long long small_work;     // ... and the last iteration touched at most this many items
     long long big_work;       // block -> grid mode when an iteration touches more
+    long long big_wave;       // block -> grid mode, inside an iteration, before a wave this large
 };
 
 struct PeelParams {
