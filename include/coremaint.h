@@ -70,7 +70,8 @@ typedef struct cm_options {
     int32_t block_threads;  /* threads per block of the peeling kernel (default 512) */
     int32_t blocks_per_sm;  /* resident blocks per SM of the persistent kernels; 0 = occupancy limit */
     int32_t max_sms;        /* SMs the persistent kernels may fill; 0 = all (lower it to share the GPU) */
-    int32_t block_mode_edges; /* single-block mode only while at most this many edges remain (16384) */
+    int32_t block_mode_edges; /* single-block mode only while at most this many edges remain (16384;
+                                 negative = never leave grid mode) */
     int64_t spin_limit_ns;  /* limit of every grid-barrier wait (default 4e9 ns); CM_ERR_LIMIT past it */
     cm_alloc_fn alloc;      /* optional allocator, see above */
     cm_free_fn free;
@@ -78,7 +79,8 @@ typedef struct cm_options {
     int32_t debug_flags;    /* test hooks, 0 in production (CM_DEBUG_*) */
     int32_t block_mode_enter; /* grid -> single block after an iteration touching <= this many items (1024) */
     int32_t block_mode_leave; /* single block -> grid after an iteration touching more (8192) */
-    int32_t reserved;
+    int32_t hub_slots;      /* grid mode: a vertex with at least this many adjacency slots is scanned by
+                               every block in chunks of 2048 (16384; negative = never) */
 } cm_options;
 
 /* Test hook: every grid barrier of the next maintenance launch waits for
@@ -225,6 +227,79 @@ int cm_multi_bases(const cm_graph* g, int32_t* bases, int32_t* ngraphs);
  * per-graph applied counts. */
 int cm_update_multi(cm_graph* g, int32_t op, const int64_t* counts, const int32_t* edges,
                     int64_t* n_applied);
+
+/* ---------------- captured update steps (many graphs, one launch) ----------------
+ * Not in the paper: the batching the method's data-parallel structure
+ * allows.  A step applies one insert batch and then one delete batch to
+ * every graph of a handle (a multi-graph handle, or a plain one with
+ * ngraphs = 1) as ONE CUDA graph replay: both batches are localised and
+ * validated, then each phase ingests its batch, relocates overfull lists
+ * behind a device-side capacity check, and runs the superior-edge-set
+ * iterations (Algorithms 1 and 5) as a conditional loop node over the
+ * grid-wide and single-block maintenance kernels.  The host only stages
+ * inputs before the replay and reads one log after it.
+ *
+ * The handle must run on a created stream (cm_set_stream / the stream of
+ * cm_create), not the legacy default stream.  Results equal two calls
+ * cm_update_multi(INSERT) then cm_update_multi(DELETE) (same selection
+ * rule, so the same iterations).  The captured graph bakes in device
+ * pointers and the configuration; the step re-captures by itself when any
+ * of them changed (buffer growth, new vertices, cm_step_set_config).  If
+ * the adjacency pool cannot take a step's relocations, the replay changes
+ * nothing and the step runs both phases on the ordinary path instead
+ * (counted as a fallback).  Destroy steps before their handle. */
+typedef struct cm_step cm_step;
+
+/* The schedule knobs a step bakes in (the autotuner's search space). */
+typedef struct cm_step_config {
+    int32_t block_mode_edges;  /* as in cm_options; negative = grid mode only */
+    int32_t block_mode_enter;
+    int32_t block_mode_leave;
+    int32_t hub_slots;         /* frontier granularity: grid-wide chunked scans from this many slots (-1 never) */
+    int32_t blocks_per_sm;     /* block shape of the grid-mode launch: resident 512-thread blocks per SM (0 = max) */
+    int32_t reserved;
+} cm_step_config;
+
+/* max_insert / max_delete: capacity (edges) of the step's two batches.
+ * cfg NULL: the handle's options.  Errors: CM_ERR_INVALID, CM_ERR_STATE
+ * (default stream, poisoned handle), CM_ERR_OOM. */
+int cm_step_create(cm_step** out, cm_graph* g, int64_t max_insert, int64_t max_delete, const cm_step_config* cfg);
+
+/* Runs one step.  ins_counts / del_counts (host, ngraphs entries, NULL =
+ * all zero): edges per graph; ins_edges / del_edges: the batches in local
+ * ids, concatenated in graph order (host or device).  ins_applied /
+ * del_applied (host, nullable, ngraphs entries) receive per-graph applied
+ * counts.  Errors: CM_ERR_CAPACITY (a batch above the step's capacity;
+ * nothing runs), CM_ERR_INVALID (an id out of range or deleted in either
+ * batch; nothing changes), CM_ERR_STATE, CM_ERR_LIMIT / CM_ERR_CUDA
+ * (poison the handle).  cm_get_stats then reports both phases together. */
+int cm_step_run(cm_step* s, const int64_t* ins_counts, const int32_t* ins_edges, const int64_t* del_counts,
+                const int32_t* del_edges, int64_t* ins_applied, int64_t* del_applied);
+
+int cm_step_get_config(const cm_step* s, cm_step_config* cfg);
+int cm_step_set_config(cm_step* s, const cm_step_config* cfg);
+/* Captures made, replays run, replays that fell back to the ordinary path. */
+int cm_step_counters(const cm_step* s, int64_t* captures, int64_t* replays, int64_t* fallbacks);
+
+typedef struct cm_tune_report {
+    cm_step_config best;
+    double best_ms;   /* median replay time of the chosen configuration */
+    double first_ms;  /* median replay time of the configuration the step had before */
+    int32_t tried;    /* configurations timed */
+    int32_t reps;     /* replays per configuration */
+} cm_tune_report;
+
+/* Autotuner: times the step's current configuration and a fixed grid of
+ * candidates (hub_slots in {4096, 16384, 65536, never} x blocks_per_sm in
+ * {1, 2} x three execution-mode threshold sets) on the given batches,
+ * `reps` replays each (median), restoring the graph's device state and the
+ * batch before every replay, and keeps the fastest on the step.  The graph
+ * is left exactly as before the call.  Needs device memory for one copy of
+ * the graph's state.  Same batch arguments and errors as cm_step_run. */
+int cm_step_autotune(cm_step* s, const int64_t* ins_counts, const int32_t* ins_edges, const int64_t* del_counts,
+                     const int32_t* del_edges, int32_t reps, cm_tune_report* report);
+
+void cm_step_destroy(cm_step* s);
 
 /* ---------------- decomposition without device allocation ----------------
  * The paper has no counterpart of this entry point; it serves callers that

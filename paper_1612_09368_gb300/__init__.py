@@ -14,6 +14,7 @@ Algorithms 5-7), vertex operations reduced to edge operations (Section I).
 from __future__ import annotations
 
 import ctypes
+import weakref
 import os
 
 import numpy as np
@@ -50,7 +51,7 @@ class cm_options(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int32), ("max_sms", ctypes.c_int32), ("block_mode_edges", ctypes.c_int32),
         ("spin_limit_ns", ctypes.c_int64), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("debug_flags", ctypes.c_int32), ("block_mode_enter", ctypes.c_int32), ("block_mode_leave", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("hub_slots", ctypes.c_int32),
     ]
 
 
@@ -68,6 +69,19 @@ class cm_stats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "phase_ns")}
         d["phase_ns"] = dict(zip(self.PHASES, list(self.phase_ns)))
         return d
+
+
+class cm_step_config(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in (
+        "block_mode_edges", "block_mode_enter", "block_mode_leave", "hub_slots", "blocks_per_sm", "reserved")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class cm_tune_report(ctypes.Structure):
+    _fields_ = [("best", cm_step_config), ("best_ms", ctypes.c_double), ("first_ms", ctypes.c_double),
+                ("tried", ctypes.c_int32), ("reps", ctypes.c_int32)]
 
 
 class CoreMaintError(RuntimeError):
@@ -114,6 +128,13 @@ def lib():
             "cm_last_error": (ctypes.c_char_p, [vp]),
             "cm_multi_bases": (ctypes.c_int, [vp, p32, p32]),
             "cm_update_multi": (ctypes.c_int, [vp, i32, p64, vp, p64]),
+            "cm_step_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, i64, i64, ctypes.POINTER(cm_step_config)]),
+            "cm_step_run": (ctypes.c_int, [vp, p64, vp, p64, vp, p64, p64]),
+            "cm_step_get_config": (ctypes.c_int, [vp, ctypes.POINTER(cm_step_config)]),
+            "cm_step_set_config": (ctypes.c_int, [vp, ctypes.POINTER(cm_step_config)]),
+            "cm_step_counters": (ctypes.c_int, [vp, p64, p64, p64]),
+            "cm_step_autotune": (ctypes.c_int, [vp, p64, vp, p64, vp, i32, ctypes.POINTER(cm_tune_report)]),
+            "cm_step_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -340,6 +361,66 @@ def cm_update_multi(h, op, counts, edges) -> np.ndarray:
     return out
 
 
+def _counts(c, ng):
+    if c is None:
+        return None, None
+    a = np.ascontiguousarray(c, dtype=np.int64)
+    if len(a) != ng:
+        raise ValueError(f"{len(a)} counts for {ng} graphs")
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), a
+
+
+def cm_step_create(h, max_insert, max_delete, config: cm_step_config | None = None):
+    s = ctypes.c_void_p()
+    _check(h, lib().cm_step_create(ctypes.byref(s), h, int(max_insert), int(max_delete),
+                                   ctypes.byref(config) if config is not None else None), "cm_step_create")
+    return s
+
+
+def cm_step_run(h, s, ng, ins_counts, ins_edges, del_counts, del_edges):
+    """Returns (per-graph inserted, per-graph deleted) as int64 arrays."""
+    ic, ick = _counts(ins_counts, ng)
+    dc, dck = _counts(del_counts, ng)
+    ip, ik = _arr(ins_edges, np.int32)
+    dp, dk = _arr(del_edges, np.int32)
+    ia = np.zeros(ng, dtype=np.int64)
+    da = np.zeros(ng, dtype=np.int64)
+    _check(h, lib().cm_step_run(s, ic, ip, dc, dp, ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                da.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "cm_step_run")
+    return ia, da
+
+
+def cm_step_autotune(h, s, ng, ins_counts, ins_edges, del_counts, del_edges, reps=2) -> dict:
+    ic, ick = _counts(ins_counts, ng)
+    dc, dck = _counts(del_counts, ng)
+    ip, ik = _arr(ins_edges, np.int32)
+    dp, dk = _arr(del_edges, np.int32)
+    r = cm_tune_report()
+    _check(h, lib().cm_step_autotune(s, ic, ip, dc, dp, int(reps), ctypes.byref(r)), "cm_step_autotune")
+    return {"best": r.best.as_dict(), "best_ms": r.best_ms, "first_ms": r.first_ms, "tried": r.tried,
+            "reps": r.reps}
+
+
+def cm_step_get_config(s) -> cm_step_config:
+    c = cm_step_config()
+    lib().cm_step_get_config(s, ctypes.byref(c))
+    return c
+
+
+def cm_step_set_config(s, config: cm_step_config):
+    lib().cm_step_set_config(s, ctypes.byref(config))
+
+
+def cm_step_counters(s) -> dict:
+    a, b, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    lib().cm_step_counters(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return {"captures": a.value, "replays": b.value, "fallbacks": c.value}
+
+
+def cm_step_destroy(s):
+    lib().cm_step_destroy(s)
+
+
 # ---------------------------------------------------------------- convenience object
 class CoreGraph:
     """Owning wrapper: a graph resident on the GPU with maintained cores."""
@@ -355,6 +436,7 @@ class CoreGraph:
             o.free = self._alloc.free
         self.options = o
         self._stream = stream
+        self._steps = weakref.WeakSet()
         if multi is not None:
             ns, ms = multi
             self._h = cm_create_multi(ns, ms, edges, cores, o, stream)
@@ -367,6 +449,8 @@ class CoreGraph:
 
     def close(self):
         if getattr(self, "_h", None):
+            for st in list(getattr(self, "_steps", ())):
+                st.close()
             cm_destroy(self._h)
             self._h = None
 
@@ -427,3 +511,46 @@ class CoreGraph:
 
     def update_multi(self, op, counts, edges) -> np.ndarray:
         return cm_update_multi(self._h, op, counts, edges)
+
+    def step(self, max_insert, max_delete, config: cm_step_config | None = None) -> "Step":
+        return Step(self, max_insert, max_delete, config)
+
+
+class Step:
+    """A captured update step of a CoreGraph (see cm_step_create): one
+    insert batch then one delete batch per graph, one CUDA graph replay."""
+
+    def __init__(self, graph: CoreGraph, max_insert, max_delete, config: cm_step_config | None = None):
+        self.graph = graph
+        self.ngraphs = len(graph.bases())
+        self._s = cm_step_create(graph.handle, max_insert, max_delete, config)
+        graph._steps.add(self)
+
+    def run(self, ins_counts=None, ins_edges=None, del_counts=None, del_edges=None):
+        return cm_step_run(self.graph.handle, self._s, self.ngraphs, ins_counts, ins_edges, del_counts, del_edges)
+
+    def autotune(self, ins_counts=None, ins_edges=None, del_counts=None, del_edges=None, reps=2) -> dict:
+        return cm_step_autotune(self.graph.handle, self._s, self.ngraphs, ins_counts, ins_edges, del_counts,
+                                del_edges, reps)
+
+    @property
+    def config(self) -> cm_step_config:
+        return cm_step_get_config(self._s)
+
+    @config.setter
+    def config(self, c: cm_step_config):
+        cm_step_set_config(self._s, c)
+
+    def counters(self) -> dict:
+        return cm_step_counters(self._s)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            cm_step_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

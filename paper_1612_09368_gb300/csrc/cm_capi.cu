@@ -6,6 +6,7 @@
 //   the edge index) -> read back counts -> relocate vertices whose slack the
 //   batch exceeds -> one cooperative launch of the maintenance kernel, which
 //   runs all superior-edge-set iterations -> read back status and counters.
+#include <algorithm>
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
@@ -21,6 +22,7 @@
 using namespace cm;
 
 static thread_local std::string g_create_err = "no error";
+constexpr int kGridThreadsHost = 512;   // threads per block of both maintenance kernels
 
 struct cm_graph {
     cm_options opt;
@@ -63,6 +65,10 @@ struct cm_graph {
     long long launches = 0;
     // execution-mode thresholds of the maintenance kernel (see cm_iterate.cu)
     long long small_edges = 16384, small_work = 1024, big_work = 8192;
+    // grid-wide chunked scans of high-degree vertices (cm_iterate.cu)
+    HubItem* HQ = nullptr;
+    HubItem* PQ = nullptr;
+    int32_t hub_len = 16384;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -149,9 +155,12 @@ static int rd_ctl(cm_graph* h) {
     return CM_OK;
 }
 
-// Reset the fields a persistent launch uses (barrier, tails, counters, stats).
+// Reset the fields a persistent launch uses (barrier, tails, counters,
+// stats).  The error word stays: an error of the ingest kernels (which the
+// host does not read back on every path) stops the maintenance kernel.
 static int reset_launch_zone(cm_graph* h) {
-    CK(h, cudaMemsetAsync(h->ctl, 0, offsetof(Ctl, nrem), h->stream));
+    CK(h, cudaMemsetAsync(h->ctl, 0, offsetof(Ctl, error), h->stream));
+    CK(h, cudaMemsetAsync(&h->ctl->tail[0], 0, offsetof(Ctl, nrem) - offsetof(Ctl, tail), h->stream));
     return CM_OK;
 }
 
@@ -161,6 +170,7 @@ static int reset_ingest_zone(cm_graph* h) {
     CK(h, cudaMemsetAsync(&h->ctl->nrem, 0, sizeof(unsigned long long) * 3, h->stream));
     CK(h, cudaMemsetAsync(&h->ctl->bad_index, 0x7F, sizeof(long long), h->stream));   // large positive
     CK(h, cudaMemsetAsync(&h->ctl->gather_n, 0, sizeof(unsigned long long), h->stream));
+    CK(h, cudaMemsetAsync(&h->ctl->defer, 0, sizeof(int), h->stream));
     return CM_OK;
 }
 
@@ -317,6 +327,7 @@ extern "C" void cm_default_options(cm_options* o) {
     o->block_mode_edges = 16384;
     o->block_mode_enter = 1024;
     o->block_mode_leave = 8192;
+    o->hub_slots = 16384;
 }
 
 static void free_all(cm_graph* h) {
@@ -342,6 +353,8 @@ static void free_all(cm_graph* h) {
     dfree(h, h->EQ, qn * 4);
     dfree(h, h->CQ, qn * 4);
     dfree(h, h->OVL, qn * 4);
+    dfree(h, h->HQ, kHubRing * sizeof(HubItem));
+    dfree(h, h->PQ, kHubRing * sizeof(HubItem));
     dfree(h, h->dbatch, (size_t)h->batch_cap * 8);
     dfree(h, h->bset, h->bset_size * sizeof(BSet));
     dfree(h, h->R0, (size_t)h->rcap * sizeof(REdge));
@@ -427,9 +440,10 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     if (h->opt.block_threads <= 0 || h->opt.block_threads > 512 || h->opt.block_threads % 32)
         h->opt.block_threads = 512;
     h->stream = (cudaStream_t)stream;
-    h->small_edges = h->opt.block_mode_edges > 0 ? h->opt.block_mode_edges : 16384;
+    h->small_edges = h->opt.block_mode_edges > 0 ? h->opt.block_mode_edges : h->opt.block_mode_edges < 0 ? 0 : 16384;
     h->small_work = h->opt.block_mode_enter > 0 ? h->opt.block_mode_enter : 1024;
     h->big_work = h->opt.block_mode_leave > 0 ? h->opt.block_mode_leave : 8192;
+    h->hub_len = h->opt.hub_slots > 0 ? h->opt.hub_slots : h->opt.hub_slots < 0 ? 0 : 16384;
     CK(h, cudaGetDevice(&h->device));
     CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     int coop = 0;
@@ -438,6 +452,9 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     for (auto& e : h->ev) CK(h, cudaEventCreate(&e));
     CK(h, cudaMalloc(&h->ctl, sizeof(Ctl)));
     CK(h, cudaMemset(h->ctl, 0, sizeof(Ctl)));
+    h->HQ = (HubItem*)dalloc(h, kHubRing * sizeof(HubItem));
+    h->PQ = (HubItem*)dalloc(h, kHubRing * sizeof(HubItem));
+    if (!h->HQ || !h->PQ) return set_err(h, CM_ERR_OOM, "out of device memory for the hub lists");
     CK(h, cudaMallocHost(&h->hctl, sizeof(Ctl)));
     memset(h->hctl, 0, sizeof(Ctl));
     h->g.slack_pct = h->opt.slack_pct;
@@ -502,6 +519,7 @@ extern "C" void cm_destroy(cm_graph* h) { free_all(h); }
 
 // ------------------------------------------------------------------ peel
 static int peel_all(cm_graph* h) {
+    CK(h, cudaMemsetAsync(&h->ctl->error, 0, sizeof(int) * 2, h->stream));
     int rc = reset_launch_zone(h);
     if (rc) return rc;
     PeelParams p{};
@@ -576,8 +594,8 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
     if (op == CM_OP_INSERT && (rc = ensure_index(h, k))) return rc;
     CK(h, cudaMemsetAsync(h->bset, 0xFF, h->bset_size * sizeof(BSet), h->stream));
     if ((rc = reset_ingest_zone(h))) return rc;
-    LAUNCH(h, ingest_a(dE, k, g, h->bset, h->bset_size - 1, h->ctl, h->stream));
-    LAUNCH(h, ingest_b(dE, k, op, g, h->bset, h->bset_size - 1, h->R0, h->OVL, h->ctl, h->stream));
+    LAUNCH(h, ingest_a(dE, k, nullptr, g, h->bset, h->bset_size - 1, h->ctl, h->stream));
+    LAUNCH(h, ingest_b(dE, k, nullptr, op, g, h->bset, h->bset_size - 1, h->R0, h->OVL, h->ctl, h->stream));
     if ((rc = rd_ctl(h))) return rc;
     Ctl& c = *h->hctl;
     if (c.error == E_INVALID)
@@ -589,7 +607,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
     const long long nrem0 = (long long)c.nrem;
     if (per_graph && h->dpergraph) {
         CK(h, cudaMemsetAsync(h->dpergraph, 0, (size_t)h->ngraphs * 8, h->stream));
-        LAUNCH(h, count_multi(h->R0, nrem0, h->dbases, h->ngraphs, h->dpergraph, h->stream));
+        LAUNCH(h, count_multi(h->R0, nrem0, nullptr, h->dbases, h->ngraphs, h->dpergraph, h->stream));
         CK(h, cudaMemcpyAsync(per_graph, h->dpergraph, (size_t)h->ngraphs * 8, cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
     }
@@ -597,15 +615,16 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         h->idx_live += nrem0;
         const long long novl = (long long)c.noverflow;
         if (novl > 0) {
-            LAUNCH(h, reloc_size(h->OVL, novl, g, h->ctl, h->stream));
+            LAUNCH(h, reloc_size(h->OVL, novl, nullptr, g, h->ctl, h->stream));
             if ((rc = rd_ctl(h))) return rc;
             if ((rc = grow_pool(h, (long long)h->hctl->reloc_need))) {
                 h->poisoned = true;
                 return rc;
             }
-            LAUNCH(h, relocate(h->OVL, novl, h->g, h->ctl, h->stream));
+            LAUNCH(h, relocate(h->OVL, novl, nullptr, h->g, h->ctl, h->stream));
         }
-        LAUNCH(h, clear_need(h->R0, nrem0, h->g, h->stream));
+        LAUNCH(h, index_new_edges(h->R0, nrem0, nullptr, h->g, h->ctl, h->stream));
+        LAUNCH(h, clear_need(h->R0, nrem0, nullptr, h->g, h->stream));
     }
     if (nrem0 > 0 && mode == 1) {
         LAUNCH(h, apply_structure(h->R0, nrem0, op, h->g, h->ctl, h->stream));
@@ -638,6 +657,9 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         p.small_work = h->small_work;
         p.big_work = h->big_work;
         p.big_wave = h->big_work / 8 > 64 ? h->big_work / 8 : 64;
+        p.HQ = h->HQ;
+        p.PQ = h->PQ;
+        p.hub_len = h->hub_len;
         int blocks, threads;
         persistent_geometry(h, 0, nrem0, &blocks, &threads);
         p.expect = (uint32_t)blocks;
@@ -992,7 +1014,7 @@ extern "C" int cm_create_multi(cm_graph** out, int32_t ngraphs, const int32_t* n
                                    is_device_ptr(edges) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(dB, bases.data(), bases.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(dP, eprefix.data(), eprefix.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok = ok && localize_multi(dE, mt, dP, dB, ngraphs, s) == cudaSuccess;
+    ok = ok && localize_multi(dE, mt, nullptr, dP, dB, ngraphs, s) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     int rc = CM_OK;
     cm_graph* h = nullptr;
@@ -1028,7 +1050,7 @@ extern "C" int cm_multi_bases(const cm_graph* h, int32_t* bases, int32_t* ngraph
     if (!h) return CM_ERR_INVALID;
     if (ngraphs) *ngraphs = h->ngraphs;
     if (bases)
-        for (int32_t i = 0; i < h->ngraphs; i++) bases[i] = h->bases[(size_t)i];
+        for (int32_t i = 0; i < h->ngraphs; i++) bases[i] = (size_t)i < h->bases.size() ? h->bases[(size_t)i] : 0;
     return CM_OK;
 }
 
@@ -1057,7 +1079,7 @@ extern "C" int cm_update_multi(cm_graph* h, int32_t op, const int64_t* counts, c
     CK(h, cudaMemcpyAsync(h->dbatch, edges, (size_t)k * 8,
                           is_device_ptr(edges) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->dprefix, pre.data(), pre.size() * 8, cudaMemcpyHostToDevice, h->stream));
-    LAUNCH(h, localize_multi(h->dbatch, k, h->dprefix, h->dbases, ng, h->stream));
+    LAUNCH(h, localize_multi(h->dbatch, k, nullptr, h->dprefix, h->dbases, ng, h->stream));
     int64_t applied = 0;
     std::vector<int64_t> per((size_t)ng, 0);
     rc = update_device(h, op, h->dbatch, k, &applied, 0, per.data());
@@ -1065,4 +1087,678 @@ extern "C" int cm_update_multi(cm_graph* h, int32_t op, const int64_t* counts, c
     if (n_applied)
         for (int32_t i = 0; i < ng; i++) n_applied[i] = per[(size_t)i];
     return end_call(h, CM_OK);
+}
+
+// ------------------------------------------------------------------ captured update steps
+// A step applies one insert batch and then one delete batch to every graph
+// of a handle as ONE CUDA graph: localisation and validation of both
+// batches, then per phase ingest, relocation behind a device-side capacity
+// gate, and the maintenance launch pairs as the body of a conditional WHILE
+// node that the single-block kernel drives.  Nothing returns to the host
+// between the step's kernels; the host stages inputs before the replay and
+// reads one log after it.  The device pointers and kernel parameters are
+// baked in at capture, so a change of any of them (growth of a buffer, new
+// vertices, another configuration) triggers a re-capture before the replay.
+
+struct StepSig {   // everything a captured step bakes in
+    DevGraph g;
+    BSet* bset;
+    unsigned long long bset_size;
+    REdge* R0;
+    REdge* R1;
+    int32_t* VQ;
+    int32_t* EQ;
+    int32_t* CQ;
+    int32_t* OVL;
+    unsigned long long qmask;
+    cudaStream_t stream;
+    cm_step_config cfg;
+};
+
+struct cm_step {
+    cm_graph* h = nullptr;
+    long long max_ins = 0, max_del = 0;
+    int32_t ng = 1;
+    cm_step_config cfg{};
+    cudaStream_t cs = nullptr, cs2 = nullptr;   // capture streams
+    int32_t* dE[2] = {nullptr, nullptr};
+    long long* dPre = nullptr;                 // 2 x (ng + 1)
+    unsigned long long* dK = nullptr;          // 2
+    unsigned long long* dPer = nullptr;        // 2 x ng
+    StepLog* dLog = nullptr;
+    long long* hPre = nullptr;                 // pinned mirrors
+    unsigned long long* hK = nullptr;
+    unsigned long long* hPer = nullptr;
+    StepLog* hLog = nullptr;
+    uint32_t* hEpoch = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    StepSig sig{};
+    bool captured = false;
+    long long captures = 0, replays = 0, fallbacks = 0;
+};
+
+static void step_default_config(const cm_graph* h, cm_step_config* c) {
+    memset(c, 0, sizeof(*c));
+    c->block_mode_edges = (int32_t)(h->small_edges > 0 ? h->small_edges : -1);
+    c->block_mode_enter = (int32_t)h->small_work;
+    c->block_mode_leave = (int32_t)h->big_work;
+    c->hub_slots = h->hub_len > 0 ? h->hub_len : -1;
+    c->blocks_per_sm = 0;
+}
+
+static StepSig step_signature(const cm_step* s) {
+    StepSig z;
+    memset(&z, 0, sizeof(z));
+    const cm_graph* h = s->h;
+    z.g = h->g;
+    z.g.n = h->n;
+    z.bset = h->bset;
+    z.bset_size = h->bset_size;
+    z.R0 = h->R0;
+    z.R1 = h->R1;
+    z.VQ = h->VQ;
+    z.EQ = h->EQ;
+    z.CQ = h->CQ;
+    z.OVL = h->OVL;
+    z.qmask = h->qmask;
+    z.stream = h->stream;
+    z.cfg = s->cfg;
+    return z;
+}
+
+static void step_release_graph(cm_step* s) {
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->exec = nullptr;
+    s->graph = nullptr;
+    s->captured = false;
+}
+
+static MaintainParams step_params(const cm_step* s, int op, int* blocks, int* threads) {
+    const cm_graph* h = s->h;
+    const cm_step_config& c = s->cfg;
+    MaintainParams p{};
+    p.g = h->g;
+    p.g.n = h->n;
+    p.ctl = h->ctl;
+    p.R0 = h->R0;
+    p.R1 = h->R1;
+    p.VQ = h->VQ;
+    p.EQ = h->EQ;
+    p.CQ = h->CQ;
+    p.qmask = h->qmask;
+    p.op = op;
+    p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
+    p.max_iters = (op == CM_OP_INSERT ? s->max_ins : s->max_del) + 1;
+    p.small_edges = c.block_mode_edges > 0 ? c.block_mode_edges : c.block_mode_edges < 0 ? 0 : 16384;
+    p.small_work = c.block_mode_enter > 0 ? c.block_mode_enter : 1024;
+    p.big_work = c.block_mode_leave > 0 ? c.block_mode_leave : 8192;
+    p.big_wave = p.big_work / 8 > 64 ? p.big_work / 8 : 64;
+    p.HQ = h->HQ;
+    p.PQ = h->PQ;
+    p.hub_len = c.hub_slots > 0 ? c.hub_slots : c.hub_slots < 0 ? 0 : 16384;
+    int occ = maintain_blocks_per_sm(kGridThreadsHost);
+    if (occ < 1) occ = 1;
+    int bps = c.blocks_per_sm > 0 && c.blocks_per_sm < occ ? c.blocks_per_sm : occ;
+    int sms = h->opt.max_sms > 0 && h->opt.max_sms < h->num_sms ? h->opt.max_sms : h->num_sms;
+    *blocks = sms * bps;
+    *threads = kGridThreadsHost;
+    p.expect = (uint32_t)*blocks;
+    return p;
+}
+
+// Adds the maintenance loop of one phase to the capture on s->cs: a WHILE
+// node whose body is the grid-mode launch and the single-block launch.
+static cudaError_t capture_loop(cm_step* s, int op) {
+    cudaStreamCaptureStatus st;
+    unsigned long long id = 0;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s->cs, &st, &id, &cg, &deps, &edata, &nd);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphConditionalHandle hc;
+    if ((e = cudaGraphConditionalHandleCreate(&hc, cg, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, cg, deps, edata, nd, &cp)) != cudaSuccess) return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(s->cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return e;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(s->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+        cudaSuccess)
+        return e;
+    int blocks = 0, threads = 0;
+    MaintainParams p = step_params(s, op, &blocks, &threads);
+    p.use_cond = 1;
+    p.cond = (unsigned long long)hc;
+    cudaError_t e1 = launch_maintain(p, blocks, threads, s->cs2);
+    cudaError_t e2 = e1 == cudaSuccess ? launch_maintain_block(p, kGridThreadsHost, s->cs2) : e1;
+    cudaGraph_t out = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(s->cs2, &out);
+    return e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
+}
+
+static cudaError_t capture_phase(cm_step* s, int phase) {
+    cm_graph* h = s->h;
+    const int op = phase == 0 ? CM_OP_INSERT : CM_OP_DELETE;
+    const long long kmax = phase == 0 ? s->max_ins : s->max_del;
+    cudaStream_t cs = s->cs;
+    DevGraph g = h->g;
+    g.n = h->n;
+    cudaError_t e;
+    unsigned long long* kp = s->dK + phase;
+    unsigned long long* np = &h->ctl->nrem;
+    if ((e = phase_begin(h->ctl, s->dLog, phase, cs)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(h->bset, 0xFF, h->bset_size * sizeof(BSet), cs)) != cudaSuccess) return e;
+    if ((e = ingest_a(s->dE[phase], kmax, kp, g, h->bset, h->bset_size - 1, h->ctl, cs)) != cudaSuccess) return e;
+    if ((e = ingest_b(s->dE[phase], kmax, kp, op, g, h->bset, h->bset_size - 1, h->R0, h->OVL, h->ctl, cs)) !=
+        cudaSuccess)
+        return e;
+    if (h->dbases) {
+        if ((e = cudaMemsetAsync(s->dPer + (size_t)phase * s->ng, 0, (size_t)s->ng * 8, cs)) != cudaSuccess) return e;
+        if ((e = count_multi(h->R0, kmax, np, h->dbases, s->ng, s->dPer + (size_t)phase * s->ng, cs)) != cudaSuccess)
+            return e;
+    }
+    if (op == CM_OP_INSERT) {
+        if ((e = reloc_size(h->OVL, 2 * kmax, &h->ctl->noverflow, g, h->ctl, cs)) != cudaSuccess) return e;
+        if ((e = reloc_gate(g, h->ctl, s->dLog, phase, cs)) != cudaSuccess) return e;
+        if ((e = relocate(h->OVL, 2 * kmax, &h->ctl->noverflow, g, h->ctl, cs)) != cudaSuccess) return e;
+        // relocation moved rows: the kernels below read offsets from memory, not from g
+        if ((e = index_new_edges(h->R0, kmax, np, g, h->ctl, cs)) != cudaSuccess) return e;
+        if ((e = clear_need(h->R0, kmax, np, g, cs)) != cudaSuccess) return e;
+    }
+    if ((e = phase_maintain(h->ctl, s->dLog, phase, cs)) != cudaSuccess) return e;
+    if ((e = capture_loop(s, op)) != cudaSuccess) return e;
+    return phase_end(h->ctl, s->dLog, phase, cs);
+}
+
+static int step_capture(cm_step* s) {
+    cm_graph* h = s->h;
+    step_release_graph(s);
+    DevGraph g = h->g;
+    g.n = h->n;
+    cudaError_t e = cudaStreamBeginCapture(s->cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) e = step_begin(h->ctl, s->dLog, s->cs);
+    for (int p = 0; p < 2 && e == cudaSuccess; p++) {
+        const long long kmax = p == 0 ? s->max_ins : s->max_del;
+        if (kmax <= 0) continue;
+        if (h->dbases)
+            e = localize_multi(s->dE[p], kmax, s->dK + p, s->dPre + (size_t)p * (s->ng + 1), h->dbases, s->ng, s->cs);
+        if (e == cudaSuccess) e = validate_pairs(s->dE[p], kmax, s->dK + p, p, g, h->ctl, s->cs);
+    }
+    for (int p = 0; p < 2 && e == cudaSuccess; p++)
+        if ((p == 0 ? s->max_ins : s->max_del) > 0) e = capture_phase(s, p);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s->cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->exec, graph, 0);
+    s->graph = graph;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        step_release_graph(s);
+        return fail_cuda(h, e, "capturing the update step");
+    }
+    s->sig = step_signature(s);
+    s->captured = true;
+    s->captures++;
+    return CM_OK;
+}
+
+extern "C" int cm_step_create(cm_step** out, cm_graph* h, int64_t max_insert, int64_t max_delete,
+                              const cm_step_config* cfg) {
+    if (!out || !h || max_insert < 0 || max_delete < 0 || max_insert + max_delete == 0)
+        return h ? set_err(h, CM_ERR_INVALID, "bad step arguments") : CM_ERR_INVALID;
+    *out = nullptr;
+    if (h->poisoned) return set_err(h, CM_ERR_STATE, "handle poisoned by an earlier failure: %s", h->err.c_str());
+    if (h->stream == nullptr || h->stream == cudaStreamLegacy)
+        return set_err(h, CM_ERR_STATE, "a captured step needs a handle on a created (non-default) stream");
+    cm_step* s = new (std::nothrow) cm_step();
+    if (!s) return set_err(h, CM_ERR_OOM, "out of host memory");
+    s->h = h;
+    s->max_ins = max_insert;
+    s->max_del = max_delete;
+    s->ng = h->ngraphs;
+    if (cfg) s->cfg = *cfg; else step_default_config(h, &s->cfg);
+    const long long kmax = max_insert > max_delete ? max_insert : max_delete;
+    int rc = ensure_batch(h, kmax);
+    bool ok = rc == CM_OK;
+    ok = ok && cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&s->cs2, cudaStreamNonBlocking) == cudaSuccess;
+    for (int p = 0; p < 2 && ok; p++) {
+        const long long k = p == 0 ? max_insert : max_delete;
+        s->dE[p] = (int32_t*)dalloc(h, (size_t)(k > 0 ? k : 1) * 8);
+        ok = s->dE[p] != nullptr;
+    }
+    ok = ok && cudaMalloc(&s->dPre, (size_t)2 * (s->ng + 1) * 8) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->dK, 2 * 8) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->dPer, (size_t)2 * s->ng * 8) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->dLog, sizeof(StepLog)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&s->hPre, (size_t)2 * (s->ng + 1) * 8) == cudaSuccess;
+    ok = ok && cudaMallocHost(&s->hK, 2 * 8) == cudaSuccess;
+    ok = ok && cudaMallocHost(&s->hPer, (size_t)2 * s->ng * 8) == cudaSuccess;
+    ok = ok && cudaMallocHost(&s->hLog, sizeof(StepLog)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&s->hEpoch, 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cm_step_destroy(s);
+        return rc ? rc : set_err(h, CM_ERR_OOM, "out of memory for an update step");
+    }
+    *out = s;
+    return CM_OK;
+}
+
+extern "C" void cm_step_destroy(cm_step* s) {
+    if (!s) return;
+    if (s->h && s->h->stream) cudaStreamSynchronize(s->h->stream);
+    step_release_graph(s);
+    if (s->h) {
+        for (int p = 0; p < 2; p++) {
+            const long long k = p == 0 ? s->max_ins : s->max_del;
+            dfree(s->h, s->dE[p], (size_t)(k > 0 ? k : 1) * 8);
+        }
+    }
+    if (s->dPre) cudaFree(s->dPre);
+    if (s->dK) cudaFree(s->dK);
+    if (s->dPer) cudaFree(s->dPer);
+    if (s->dLog) cudaFree(s->dLog);
+    if (s->hPre) cudaFreeHost(s->hPre);
+    if (s->hK) cudaFreeHost(s->hK);
+    if (s->hPer) cudaFreeHost(s->hPer);
+    if (s->hLog) cudaFreeHost(s->hLog);
+    if (s->hEpoch) cudaFreeHost(s->hEpoch);
+    if (s->cs) cudaStreamDestroy(s->cs);
+    if (s->cs2) cudaStreamDestroy(s->cs2);
+    delete s;
+}
+
+extern "C" int cm_step_get_config(const cm_step* s, cm_step_config* cfg) {
+    if (!s || !cfg) return CM_ERR_INVALID;
+    *cfg = s->cfg;
+    return CM_OK;
+}
+
+extern "C" int cm_step_set_config(cm_step* s, const cm_step_config* cfg) {
+    if (!s || !cfg) return CM_ERR_INVALID;
+    s->cfg = *cfg;   // re-captured before the next replay
+    return CM_OK;
+}
+
+extern "C" int cm_step_counters(const cm_step* s, int64_t* captures, int64_t* replays, int64_t* fallbacks) {
+    if (!s) return CM_ERR_INVALID;
+    if (captures) *captures = s->captures;
+    if (replays) *replays = s->replays;
+    if (fallbacks) *fallbacks = s->fallbacks;
+    return CM_OK;
+}
+
+// Stages one step's batches into the step's buffers (local ids, graph
+// order) and its counts; returns the batch sizes.
+static int step_stage(cm_step* s, const int64_t* const counts[2], const int32_t* const edges[2], long long k[2]) {
+    cm_graph* h = s->h;
+    for (int p = 0; p < 2; p++) {
+        long long* pre = s->hPre + (size_t)p * (s->ng + 1);
+        pre[0] = 0;
+        for (int32_t i = 0; i < s->ng; i++) {
+            const long long c = counts[p] ? counts[p][i] : 0;
+            if (c < 0) return set_err(h, CM_ERR_INVALID, "negative count for graph %d", i);
+            pre[i + 1] = pre[i] + c;
+        }
+        k[p] = pre[s->ng];
+        if (k[p] > (p == 0 ? s->max_ins : s->max_del))
+            return set_err(h, CM_ERR_CAPACITY, "%s batch of %lld edges exceeds the step's capacity",
+                           p == 0 ? "insert" : "delete", k[p]);
+        if (k[p] > 0 && !edges[p]) return set_err(h, CM_ERR_INVALID, "NULL edges");
+        s->hK[p] = (unsigned long long)k[p];
+    }
+    for (int p = 0; p < 2; p++) {
+        if (k[p] > 0)
+            CK(h, cudaMemcpyAsync(s->dE[p], edges[p], (size_t)k[p] * 8,
+                                  is_device_ptr(edges[p]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream));
+    }
+    CK(h, cudaMemcpyAsync(s->dPre, s->hPre, (size_t)2 * (s->ng + 1) * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(s->dK, s->hK, 16, cudaMemcpyHostToDevice, h->stream));
+    return CM_OK;
+}
+
+// Host-side preconditions of a replay; re-captures when anything baked in changed.
+static int step_prepare(cm_step* s, long long kins) {
+    cm_graph* h = s->h;
+    int rc;
+    if ((rc = ensure_index(h, kins))) return rc;
+    const long long kmax = s->max_ins > s->max_del ? s->max_ins : s->max_del;
+    if ((rc = ensure_batch(h, kmax))) return rc;
+    if (h->epoch > 0x3F000000u) {   // 30-bit stamps about to wrap: clear them
+        DevGraph& g = h->g;
+        CK(h, cudaMemsetAsync(g.chg, 0, (size_t)h->n * 4, h->stream));
+        CK(h, cudaMemsetAsync(g.taken, 0, (size_t)h->n * 4, h->stream));
+        CK(h, cudaMemset2DAsync((char*)g.hs + 8, sizeof(int4), 0, 8, (size_t)h->n, h->stream));
+        h->epoch = 1;
+    }
+    *s->hEpoch = h->epoch;
+    CK(h, cudaMemcpyAsync(&h->ctl->rs.epoch, s->hEpoch, 4, cudaMemcpyHostToDevice, h->stream));
+    StepSig now = step_signature(s);
+    if (!s->captured || memcmp(&now, &s->sig, sizeof(StepSig)) != 0) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        if ((rc = step_capture(s))) return rc;
+    }
+    return CM_OK;
+}
+
+// Reads the log of a replay and brings the host mirrors up to date.  If the
+// pool could not take the insert phase's relocations, the step stopped
+// before changing anything and both phases run on the ordinary path.
+static int step_finish(cm_step* s, const long long k[2], int64_t* applied[2]) {
+    cm_graph* h = s->h;
+    CK(h, cudaMemcpyAsync(s->hLog, s->dLog, sizeof(StepLog), cudaMemcpyDeviceToHost, h->stream));
+    if (h->dbases)
+        CK(h, cudaMemcpyAsync(s->hPer, s->dPer, (size_t)2 * s->ng * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const StepLog& L = *s->hLog;
+    const Ctl& c = *h->hctl;
+    for (int p = 0; p < 2; p++) {
+        if (L.error[p] == E_INVALID || (L.defer == p + 1 && c.error == E_INVALID)) {
+            const long long bi = c.bad_index;
+            return set_err(h, CM_ERR_INVALID, "edge %lld of the %s batch names a vertex out of range or deleted",
+                           bi & ((1ll << 40) - 1), (bi >> 40) ? "delete" : "insert");
+        }
+    }
+    if (c.error == E_INVALID) {
+        const long long bi = c.bad_index;
+        return set_err(h, CM_ERR_INVALID, "edge %lld of the %s batch names a vertex out of range or deleted",
+                       bi & ((1ll << 40) - 1), (bi >> 40) ? "delete" : "insert");
+    }
+    if (c.error) {
+        h->poisoned = true;
+        return set_err(h, CM_ERR_LIMIT, "captured step stopped with device error %d", c.error);
+    }
+    h->epoch = L.epoch_end;
+    cm_stats& st = h->last;
+    for (int p = 0; p < 2; p++) {
+        const bool ran = L.defer == 0 || L.defer > p + 1;
+        if (!ran) break;
+        const long long kept = (long long)L.kept[p];
+        if (p == 0) {
+            h->idx_live += kept;
+            h->m += kept;
+        } else {
+            h->idx_live -= kept;
+            h->idx_tomb += kept;
+            h->m -= kept;
+        }
+        st.applied += kept;
+        st.iterations += (int64_t)L.st[p][ST_ITERS];
+        st.select_rounds += (int64_t)L.st[p][ST_ROUNDS];
+        st.selected += (int64_t)L.st[p][ST_SELECTED];
+        st.remaining_sum += (int64_t)L.st[p][ST_REMSUM];
+        st.visited += (int64_t)L.st[p][ST_VISITED];
+        st.visited_slots += (int64_t)L.st[p][ST_VISSLOTS];
+        st.evicted += (int64_t)L.st[p][ST_EVICTED];
+        st.evicted_slots += (int64_t)L.st[p][ST_EVSLOTS];
+        st.changed += (int64_t)L.st[p][ST_CHANGED];
+        st.changed_slots += (int64_t)L.st[p][ST_CHSLOTS];
+        st.waves += (int64_t)L.st[p][ST_WAVES];
+        st.barriers += (int64_t)L.st[p][ST_BARRIERS];
+        st.grid_iterations += (int64_t)L.st[p][ST_GRID_ITERS];
+        for (int i = 0; i < PH_COUNT && i < 7; i++) st.phase_ns[i] += (int64_t)L.ph[p][i];
+        st.alg_bytes += 16 * (int64_t)L.st[p][ST_REMSUM] + 16 * (int64_t)L.st[p][ST_SELECTED] +
+                        16 * (int64_t)L.st[p][ST_VISITED] + 12 * (int64_t)L.st[p][ST_VISSLOTS] +
+                        12 * (int64_t)L.st[p][ST_EVSLOTS] + 8 * (int64_t)L.st[p][ST_CHANGED] +
+                        8 * (int64_t)L.st[p][ST_CHSLOTS];
+        if (applied[p]) {
+            if (h->dbases) {
+                for (int32_t i = 0; i < s->ng; i++) applied[p][i] = (int64_t)s->hPer[(size_t)p * s->ng + i];
+            } else {
+                applied[p][0] = kept;
+            }
+        }
+    }
+    if (L.defer == 1) {   // pool short: ordinary path for both phases (the graph is unchanged)
+        s->fallbacks++;
+        for (int p = 0; p < 2; p++) {
+            if (k[p] == 0) {
+                if (applied[p])
+                    for (int32_t i = 0; i < s->ng; i++) applied[p][i] = 0;
+                continue;
+            }
+            std::vector<int64_t> per((size_t)s->ng, 0);
+            int64_t a = 0;
+            int rc = update_device(h, p == 0 ? CM_OP_INSERT : CM_OP_DELETE, s->dE[p], k[p], &a, 0,
+                                   h->dbases ? per.data() : nullptr);
+            if (rc) return rc;
+            if (applied[p]) {
+                if (h->dbases) {
+                    for (int32_t i = 0; i < s->ng; i++) applied[p][i] = per[(size_t)i];
+                } else {
+                    applied[p][0] = a;
+                }
+            }
+        }
+    }
+    return CM_OK;
+}
+
+static int step_run_staged(cm_step* s, const long long k[2], int64_t* applied[2]) {
+    cm_graph* h = s->h;
+    int rc = step_prepare(s, k[0]);
+    if (rc) return rc;
+    CK(h, cudaEventRecord(h->ev[2], h->stream));
+    CK(h, cudaGraphLaunch(s->exec, h->stream));
+    CK(h, cudaEventRecord(h->ev[3], h->stream));
+    s->replays++;
+    h->launches += 1;
+    rc = step_finish(s, k, applied);
+    if (rc) return rc;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+    h->last.maintain_ms += ms;
+    return CM_OK;
+}
+
+extern "C" int cm_step_run(cm_step* s, const int64_t* ins_counts, const int32_t* ins_edges,
+                           const int64_t* del_counts, const int32_t* del_edges, int64_t* ins_applied,
+                           int64_t* del_applied) {
+    if (!s) return CM_ERR_INVALID;
+    cm_graph* h = s->h;
+    int rc = begin_call(h);
+    if (rc) return rc;
+    if (h->cores_stale) return end_call(h, set_err(h, CM_ERR_STATE, "cores are stale: call cm_recompute_cores"));
+    const int64_t* counts[2] = {ins_counts, del_counts};
+    const int32_t* edges[2] = {ins_edges, del_edges};
+    long long k[2];
+    if ((rc = step_stage(s, counts, edges, k))) return end_call(h, rc);
+    int64_t* applied[2] = {ins_applied, del_applied};
+    return end_call(h, step_run_staged(s, k, applied));
+}
+
+// ------------------------------------------------------------------ autotuner
+// Times candidate configurations of a step on a real batch: the graph's
+// state is saved once, and before every trial the state and the raw batch
+// are restored, so each trial replays the same work from the same graph.
+struct Snapshot {
+    size_t nv = 0, adj = 0, idx = 0;
+    int4* hs = nullptr;
+    int64_t* off = nullptr;
+    int32_t* i32 = nullptr;        // end, cap, deg, chg, taken (5 x nv)
+    unsigned long long* claims = nullptr;   // claim0, claim1 (2 x nv)
+    int32_t* pool = nullptr;
+    Bucket* index = nullptr;
+    Ctl* ctl = nullptr;
+    int64_t m = 0, idx_live = 0, idx_tomb = 0;
+    uint32_t epoch = 0;
+    int32_t n = 0;
+};
+
+static void snap_free(cm_graph* h, Snapshot& z) {
+    dfree(h, z.hs, z.nv * sizeof(int4));
+    dfree(h, z.off, z.nv * 8);
+    dfree(h, z.i32, z.nv * 4 * 5);
+    dfree(h, z.claims, z.nv * 8 * 2);
+    dfree(h, z.pool, z.adj * 4);
+    dfree(h, z.index, z.idx * sizeof(Bucket));
+    dfree(h, z.ctl, sizeof(Ctl));
+    z = Snapshot{};
+}
+
+static int snap_copy(cm_graph* h, Snapshot& z, bool save) {
+    DevGraph& g = h->g;
+    const cudaMemcpyKind kd = cudaMemcpyDeviceToDevice;
+    cudaStream_t st = h->stream;
+    auto cp = [&](void* snap, void* live, size_t bytes) {
+        return save ? cudaMemcpyAsync(snap, live, bytes, kd, st) : cudaMemcpyAsync(live, snap, bytes, kd, st);
+    };
+    const size_t nv = z.nv;
+    CK(h, cp(z.hs, g.hs, nv * sizeof(int4)));
+    CK(h, cp(z.off, g.off, nv * 8));
+    CK(h, cp(z.i32 + 0 * nv, g.end, nv * 4));
+    CK(h, cp(z.i32 + 1 * nv, g.cap, nv * 4));
+    CK(h, cp(z.i32 + 2 * nv, g.deg, nv * 4));
+    CK(h, cp(z.i32 + 3 * nv, g.chg, nv * 4));
+    CK(h, cp(z.i32 + 4 * nv, g.taken, nv * 4));
+    CK(h, cp(z.claims, g.claim0, nv * 8));
+    CK(h, cp(z.claims + nv, g.claim1, nv * 8));
+    if (z.adj) CK(h, cp(z.pool, g.adj, z.adj * 4));
+    CK(h, cp(z.index, g.idx, z.idx * sizeof(Bucket)));
+    CK(h, cp(z.ctl, h->ctl, sizeof(Ctl)));
+    if (save) {
+        z.m = h->m;
+        z.idx_live = h->idx_live;
+        z.idx_tomb = h->idx_tomb;
+        z.epoch = h->epoch;
+        z.n = h->n;
+    } else {
+        h->m = z.m;
+        h->idx_live = z.idx_live;
+        h->idx_tomb = z.idx_tomb;
+        h->epoch = z.epoch;
+        h->n = z.n;
+    }
+    return CM_OK;
+}
+
+static int snap_take(cm_graph* h, Snapshot& z) {
+    CK(h, cudaMemcpyAsync(&h->hctl->adj_top, &h->ctl->adj_top, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    z.nv = (size_t)h->n;
+    z.adj = (size_t)h->hctl->adj_top;
+    z.idx = (size_t)h->idx_size;
+    z.hs = (int4*)dalloc(h, z.nv * sizeof(int4));
+    z.off = (int64_t*)dalloc(h, z.nv * 8);
+    z.i32 = (int32_t*)dalloc(h, z.nv * 4 * 5);
+    z.claims = (unsigned long long*)dalloc(h, z.nv * 8 * 2);
+    z.pool = (int32_t*)dalloc(h, z.adj * 4);
+    z.index = (Bucket*)dalloc(h, z.idx * sizeof(Bucket));
+    z.ctl = (Ctl*)dalloc(h, sizeof(Ctl));
+    if (!z.hs || !z.off || !z.i32 || !z.claims || !z.pool || !z.index || !z.ctl) {
+        snap_free(h, z);
+        return set_err(h, CM_ERR_OOM, "out of device memory for the tuner's copy of the graph");
+    }
+    return snap_copy(h, z, true);
+}
+
+extern "C" int cm_step_autotune(cm_step* s, const int64_t* ins_counts, const int32_t* ins_edges,
+                                const int64_t* del_counts, const int32_t* del_edges, int32_t reps,
+                                cm_tune_report* report) {
+    if (!s) return CM_ERR_INVALID;
+    cm_graph* h = s->h;
+    int rc = begin_call(h);
+    if (rc) return rc;
+    if (h->cores_stale) return end_call(h, set_err(h, CM_ERR_STATE, "cores are stale"));
+    if (reps < 1) reps = 1;
+    const int64_t* counts[2] = {ins_counts, del_counts};
+    const int32_t* edges[2] = {ins_edges, del_edges};
+    long long k[2];
+    if ((rc = step_stage(s, counts, edges, k))) return end_call(h, rc);
+    // every buffer the step uses is in place before the graph is saved, so
+    // no trial reallocates and every trial sees the same pointers
+    if ((rc = ensure_index(h, k[0]))) return end_call(h, rc);
+    // keep the raw batches: the step localises them in place
+    int32_t* raw[2] = {nullptr, nullptr};
+    for (int p = 0; p < 2; p++) {
+        if (k[p] == 0) continue;
+        raw[p] = (int32_t*)dalloc(h, (size_t)k[p] * 8);
+        if (!raw[p]) {
+            dfree(h, raw[0], (size_t)k[0] * 8);
+            return end_call(h, set_err(h, CM_ERR_OOM, "out of device memory for the tuner's batch copy"));
+        }
+        CK(h, cudaMemcpyAsync(raw[p], s->dE[p], (size_t)k[p] * 8, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    Snapshot z;
+    if ((rc = snap_take(h, z))) {
+        for (int p = 0; p < 2; p++) dfree(h, raw[p], (size_t)k[p] * 8);
+        return end_call(h, rc);
+    }
+    // candidates: frontier granularity (hub threshold) x block shape
+    // (resident blocks per SM) x execution-mode thresholds
+    const int32_t hubs[] = {4096, 16384, 65536, -1};
+    const int32_t bps[] = {1, 2};
+    const int32_t modes[][3] = {{16384, 1024, 8192}, {65536, 4096, 32768}, {-1, 1024, 8192}};
+    std::vector<cm_step_config> cand;
+    const cm_step_config first = s->cfg;
+    cand.push_back(first);
+    for (int32_t hb : hubs)
+        for (int32_t b : bps)
+            for (const auto& md : modes) {
+                cm_step_config c{};
+                c.hub_slots = hb;
+                c.blocks_per_sm = b;
+                c.block_mode_edges = md[0];
+                c.block_mode_enter = md[1];
+                c.block_mode_leave = md[2];
+                cand.push_back(c);
+            }
+    double best_ms = 1e30, first_ms = 0;
+    cm_step_config best = first;
+    int tried = 0;
+    int64_t* none[2] = {nullptr, nullptr};
+    std::vector<float> t;
+    for (size_t ci = 0; ci < cand.size() && rc == CM_OK; ci++) {
+        s->cfg = cand[ci];
+        t.clear();
+        for (int r = 0; r < reps && rc == CM_OK; r++) {
+            if ((rc = snap_copy(h, z, false))) break;
+            for (int p = 0; p < 2; p++)
+                if (k[p]) CK(h, cudaMemcpyAsync(s->dE[p], raw[p], (size_t)k[p] * 8, cudaMemcpyDeviceToDevice, h->stream));
+            CK(h, cudaMemcpyAsync(s->dPre, s->hPre, (size_t)2 * (s->ng + 1) * 8, cudaMemcpyHostToDevice, h->stream));
+            CK(h, cudaMemcpyAsync(s->dK, s->hK, 16, cudaMemcpyHostToDevice, h->stream));
+            memset(&h->last, 0, sizeof(h->last));
+            if ((rc = step_run_staged(s, k, none))) break;
+            t.push_back((float)h->last.maintain_ms);
+        }
+        if (rc) break;
+        std::sort(t.begin(), t.end());
+        const double med = t[t.size() / 2];
+        tried++;
+        if (ci == 0) first_ms = med;
+        if (med < best_ms) {
+            best_ms = med;
+            best = cand[ci];
+        }
+    }
+    // leave the graph as it was before tuning and the step on the winner
+    int rc2 = snap_copy(h, z, false);
+    CK(h, cudaStreamSynchronize(h->stream));
+    snap_free(h, z);
+    for (int p = 0; p < 2; p++) dfree(h, raw[p], (size_t)k[p] * 8);
+    s->cfg = rc == CM_OK ? best : first;
+    if (rc == CM_OK) rc = rc2;
+    if (rc == CM_OK && report) {
+        report->best = best;
+        report->best_ms = best_ms;
+        report->first_ms = first_ms;
+        report->tried = tried;
+        report->reps = reps;
+    }
+    memset(&h->last, 0, sizeof(h->last));
+    return end_call(h, rc);
 }

@@ -73,6 +73,27 @@ struct Resume {
     unsigned long long vq0, eq0, cq0, flo, fhi, elo, ehi;
 };
 
+constexpr int kTails = 6;
+
+// A vertex whose adjacency is scanned by every block of a grid-mode launch,
+// in chunks of kChunk slots (48 bytes; the lists are rings of kHubRing).
+// kind: HUB_FRONT (insert frontier: chunks sum CSD, the last one decides),
+// HUB_EVICT_INS / HUB_EVICT_DEL (eviction scans), HUB_EXPAND (visit the
+// frontier neighbours of a hub whose support stayed above k).
+enum { HUB_FRONT = 0, HUB_EVICT_INS = 1, HUB_EVICT_DEL = 2, HUB_EXPAND = 3 };
+struct __align__(16) HubItem {
+    long long off;                 // adjacency offset
+    unsigned long long c0;         // first chunk (global chunk numbering of its list)
+    int32_t v, kind, k, len;
+    int32_t nch;                   // chunks
+    int32_t acc;                   // partial-sum accumulator (HUB_FRONT)
+    uint32_t done;                 // chunks finished
+    int32_t pad;
+};
+constexpr int kChunk = 2048;                // slots per chunk: one 4-wide pass of 512 threads
+constexpr unsigned long long kHubRing = 1ull << 16;
+constexpr unsigned long long kHubRingSafe = 1ull << 15;   // producers stop short of this backlog
+
 // Device control block, one per handle.  The barrier words and counters are
 // 64-bit and monotone within a launch where noted.
 struct __align__(128) Ctl {
@@ -80,10 +101,13 @@ struct __align__(128) Ctl {
     unsigned long long release;    // grid barrier: released generation
     int error;                     // first device error (E_*)
     int err_info;
-    unsigned long long tail[4];    // ring tails: 0 VQ, 1 EQ, 2 CQ, 3 spare (monotone in a launch)
-    unsigned long long pc[4];      // phase counters, copied to spc and zeroed at every barrier
-    unsigned long long stail[4];   // snapshot of tail at the last barrier
-    unsigned long long spc[4];     // snapshot of pc at the last barrier
+    // ring tails (monotone in a call): 0 VQ, 1 EQ, 2 CQ, 3 spare, 4 / 5 the
+    // hub and expansion item lists, packed (items << 40 | chunks)
+    unsigned long long tail[kTails];
+    unsigned long long pc[kTails];     // phase counters, copied to spc and zeroed at every barrier
+    unsigned long long stail[kTails];  // snapshot of tail at the last barrier
+    unsigned long long spc[kTails];    // snapshot of pc at the last barrier
+    unsigned long long sprev[2];       // stail[4], stail[5] of the barrier before the last
     unsigned long long st[ST_COUNT];
     unsigned long long ph[PH_COUNT];   // nanoseconds per phase (block 0's view)
     // ingest / host exchange
@@ -94,9 +118,22 @@ struct __align__(128) Ctl {
     long long bad_index;           // smallest invalid input position
     unsigned long long gather_n;   // gathered incident edges (vertex deletion)
     int min_deg;                   // peel: smallest remaining degree
-    int pad0;
-    unsigned long long wc;         // spare
+    int defer;                     // captured step: skip its remaining kernels (1 pool short, 2 error)
+    unsigned long long passes;     // captured step: launch pairs of the current phase
     Resume rs;
+};
+
+// What a captured update step records per phase (0 insert, 1 delete) for
+// the host to read after the replay.
+struct StepLog {
+    unsigned long long st[2][ST_COUNT];
+    unsigned long long ph[2][PH_COUNT];
+    unsigned long long kept[2];    // edges kept by ingest
+    unsigned long long passes[2];
+    long long iters_end[2];
+    int error[2];
+    int defer;                     // phase at which the step stopped (+1), 0 if it ran to the end
+    uint32_t epoch_end;
 };
 
 // Plain-old-data view of a graph passed to kernels by value.
@@ -191,7 +228,9 @@ __device__ __forceinline__ bool grid_sync(Ctl* c, unsigned int expect, unsigned 
         unsigned long long t = atomicAdd(&c->arrive, 1ull);
         unsigned long long gen = t / expect;
         if (t % expect == expect - 1) {
-            for (int i = 0; i < 4; i++) {
+            c->sprev[0] = c->stail[4];
+            c->sprev[1] = c->stail[5];
+            for (int i = 0; i < kTails; i++) {
                 c->stail[i] = vload64(&c->tail[i]);
                 c->spc[i] = vload64(&c->pc[i]);
                 c->pc[i] = 0;
@@ -223,7 +262,9 @@ __device__ __forceinline__ bool block_sync(Ctl* c) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; i++) {
+        c->sprev[0] = c->stail[4];
+        c->sprev[1] = c->stail[5];
+        for (int i = 0; i < kTails; i++) {
             c->stail[i] = vload64(&c->tail[i]);
             c->spc[i] = vload64(&c->pc[i]);
             c->pc[i] = 0;

@@ -84,16 +84,43 @@ struct Barrier {
     }
 };
 
+// ---------------------------------------------------------------- hub lists
+constexpr unsigned long long kChunkMask = (1ull << 40) - 1;
+
+// Appends a hub item to list `slot` (4: HQ, 5: PQ) unless the list's backlog
+// since item `lo_items` (the oldest item still being consumed) nears the
+// ring size.  One thread calls it.
+__device__ __forceinline__ bool push_hub(Ctl* C, HubItem* ring, int slot, unsigned long long lo_items, int v,
+                                         int kind, int k, long long off, int len) {
+    if ((vload64(&C->tail[slot]) >> 40) - lo_items >= kHubRingSafe) return false;
+    const int nch = (len + kChunk - 1) / kChunk;
+    const unsigned long long old = atomicAdd(&C->tail[slot], (1ull << 40) | (unsigned long long)nch);
+    HubItem& it = ring[(old >> 40) & (kHubRing - 1)];
+    it.off = off;
+    it.c0 = old & kChunkMask;
+    it.v = v;
+    it.kind = kind;
+    it.k = k;
+    it.len = len;
+    it.nch = nch;
+    it.acc = 0;
+    it.done = 0u;
+    return true;
+}
+
 // Runs body(v, Group) for every vertex of ring[lo, hi): one warp per vertex
 // with dynamic fetching (counter *ctr, zeroed at every barrier).  A vertex
 // with at least kBigLen slots is deferred by the warp that fetched it and
-// then processed by that warp's whole block (512 threads in either mode,
-// in single-block mode), so a hub does not hold a wave on one warp.  Every
-// thread of the launch must call it.
-template <int MODE, class Body>
-__device__ __forceinline__ void for_each_vertex(const DevGraph& g, unsigned long long* ctr, const int32_t* ring,
-                                                unsigned long long qm, unsigned long long lo, unsigned long long hi,
-                                                Body body) {
+// then processed by that warp's whole block (512 threads in either mode),
+// so a hub does not hold a wave on one warp.  In grid mode a vertex with at
+// least P.hub_len slots becomes a hub item of kind HUB instead (HUB >= 0),
+// which every block scans in chunks in the next wave.  Every thread of the
+// launch must call it.
+template <int MODE, int HUB, class Body>
+__device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P,
+                                                unsigned long long* ctr,
+                                                const int32_t* ring, unsigned long long qm, unsigned long long lo,
+                                                unsigned long long hi, Body body) {
     constexpr int NT = MODE == 0 ? kGridThreads : kBlockThreads;
     const int lane = lane_id();
     __shared__ int s_big[kMaxBig];
@@ -107,11 +134,17 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, unsigned long
         if (j >= hi - lo) break;
         const int v = ring[(lo + j) & qm];
         int defer = 0;
-        if (lane == 0 && g.end[v] >= kBigLen) {
-            int s = atomicAdd(&s_nbig, 1);
-            if (s < kMaxBig) {
-                s_big[s] = v;
+        if (lane == 0) {
+            const int len = g.end[v];
+            if (MODE == 0 && HUB >= 0 && P.hub_len > 0 && len >= P.hub_len &&
+                push_hub(C, P.HQ, 4, vload64(&C->sprev[0]) >> 40, v, HUB, g.hs[v].x, g.off[v], len)) {
                 defer = 1;
+            } else if (len >= kBigLen) {
+                int s = atomicAdd(&s_nbig, 1);
+                if (s < kMaxBig) {
+                    s_big[s] = v;
+                    defer = 1;
+                }
             }
         }
         if (__shfl_sync(0xffffffffu, defer, 0)) continue;
@@ -122,6 +155,102 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, unsigned long
     for (int b = 0; b < nb; b++) {
         body(s_big[b], BlockGroup<NT>{});
         __syncthreads();
+    }
+}
+
+// Grid mode: every block takes chunks of the hub items queued in the
+// previous wave (HQ) and of the expansion items (PQ): the ranges between the
+// last two barrier snapshots, in the packed (items << 40 | chunks) form.
+//   HUB_FRONT: the chunk's share of CSD goes to the item; the block that
+//     finishes the last chunk adds the sum to the support word at once
+//     (flagging the vertex processed, as a whole-list scan would) and either
+//     queues an expansion item (support > k) or evicts the vertex.
+//   HUB_EVICT_INS / HUB_EVICT_DEL: the chunk's share of the eviction; the
+//     last chunk lowers the core (delete) and counts the vertex.
+//   HUB_EXPAND: the chunk's share of the frontier expansion.
+// The support word tolerates the delay: decrements from evicted neighbours
+// land before or after the CSD sum in any order, and a processed hub whose
+// count later falls to k is evicted by the decrement that does it.
+__device__ __noinline__ void hub_chunks(const DevGraph& g, Ctl* C, const MaintainParams& P, uint32_t e,
+                                           LocalStats& ls) {
+    using BG = BlockGroup<kGridThreads>;
+    const unsigned long long hq_lo = vload64(&C->sprev[0]), hq_hi = vload64(&C->stail[4]);
+    const unsigned long long pq_lo = vload64(&C->sprev[1]), pq_hi = vload64(&C->stail[5]);
+    const unsigned long long nh = (hq_hi & kChunkMask) - (hq_lo & kChunkMask);
+    const unsigned long long np = (pq_hi & kChunkMask) - (pq_lo & kChunkMask);
+    if (nh + np == 0) return;
+    __shared__ unsigned long long s_j;
+    __shared__ unsigned long long s_item;
+    __shared__ int s_expand_all;
+    const int lane = lane_id();
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_j = atomicAdd(&C->pc[4], 1ull);
+        __syncthreads();
+        const unsigned long long j = s_j;
+        if (j >= nh + np) break;
+        const bool from_h = j < nh;
+        HubItem* ring = from_h ? P.HQ : P.PQ;
+        const unsigned long long gc = from_h ? (hq_lo & kChunkMask) + j : (pq_lo & kChunkMask) + (j - nh);
+        if (threadIdx.x < 32) {
+            // 32-way search for the last item whose first chunk is <= gc
+            unsigned long long lo = (from_h ? hq_lo : pq_lo) >> 40, hi = (from_h ? hq_hi : pq_hi) >> 40;
+            for (int guard = 0; guard < 16 && hi - lo > 1; guard++) {
+                const unsigned long long step = (hi - lo + 31) / 32;
+                const unsigned long long idx = lo + (unsigned long long)lane * step;
+                const bool le = idx < hi && ring[idx & (kHubRing - 1)].c0 <= gc;
+                const unsigned int b = __ballot_sync(0xffffffffu, le);
+                const int last = 31 - __clz(b);   // lane 0 always qualifies
+                lo = lo + (unsigned long long)last * step;
+                hi = min(lo + step, hi);
+            }
+            if (lane == 0) s_item = lo;
+        }
+        __syncthreads();
+        HubItem* it = &ring[s_item & (kHubRing - 1)];
+        const int v = it->v, kind = it->kind, k = it->k, len = it->len, nch = it->nch;
+        const long long off = it->off;
+        const int ci = (int)(gc - it->c0);
+        const int s0 = ci * kChunk, s1 = min(s0 + kChunk, len);
+        if (kind == HUB_FRONT) {
+            const int part = BG::sum(csd_part<BG>(g, k, off, s0, s1));
+            if (threadIdx.x == 0) {
+                s_expand_all = 0;
+                atomicAdd(&it->acc, part);
+                __threadfence();
+                if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
+                    __threadfence();
+                    const int acc = atomicAdd(&it->acc, 0);
+                    uint32_t of;
+                    int32_t oc;
+                    add_word(g, C, v, e, acc, kProcessed, of, oc);
+                    ls.vis++;
+                    ls.visl += len;
+                    if (oc + acc > k) {
+                        if (!push_hub(C, P.PQ, 5, pq_hi >> 40, v, HUB_EXPAND, k, off, len)) s_expand_all = 1;
+                    } else {
+                        const unsigned long long q = atomicAdd(&C->tail[1], 1ull);
+                        P.EQ[q & P.qmask] = v;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_expand_all) expand_range<BG>(g, C, P, k, off, 0, len, e);   // expansion list full
+        } else if (kind == HUB_EXPAND) {
+            expand_range<BG>(g, C, P, k, off, s0, s1, e);
+        } else {
+            if (kind == HUB_EVICT_INS) evict_ins_range<BG>(g, C, P, k, off, s0, s1, e);
+            else evict_del_range<BG>(g, C, P, k, off, s0, s1, e);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
+                    if (kind == HUB_EVICT_DEL) g.hs[v].x = k - 1;
+                    ls.ev++;
+                    ls.evl += len;
+                }
+            }
+        }
     }
 }
 
@@ -173,6 +302,25 @@ __device__ __forceinline__ int check_edge(const DevGraph& g, REdge* R, long long
     return 0;
 }
 
+constexpr unsigned long long kMaxPasses = 256;   // launch pairs per phase of a captured step
+
+// Inside a captured update step the launch pairs (grid kernel, then
+// single-block kernel) are the body of a conditional WHILE node: the
+// single-block kernel ends every pass by setting the node's condition, so
+// the loop runs until the call is done or failed with no host round trip.
+__device__ __forceinline__ void loop_control(const MaintainParams& P, Ctl* C) {
+    if (!P.use_cond || threadIdx.x != 0) return;
+    const unsigned long long n = C->passes + 1;
+    C->passes = n;
+    int err = vload32(&C->error);
+    const int done = *(volatile int*)&C->rs.done;
+    if (!err && !done && n >= kMaxPasses) {
+        atomicCAS(&C->error, 0, E_ITER_LIMIT);
+        err = 1;
+    }
+    cudaGraphSetConditional((cudaGraphConditionalHandle)P.cond, (!err && !done) ? 1u : 0u);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE == 0 ? 2 : 1)
     maintain_kernel(MaintainParams P) {
@@ -181,7 +329,10 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     // where to resume (the host or the other mode wrote it before this launch)
     const int done0 = *(volatile int*)&C->rs.done;
     const int want = *(volatile int*)&C->rs.want;
-    if (done0 || want != MODE || vload32(&C->error)) return;
+    if (done0 || want != MODE || vload32(&C->error)) {
+        if (MODE == 1) loop_control(P, C);
+        return;
+    }
     const int lane = lane_id();
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -195,6 +346,11 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     uint32_t e = *(volatile uint32_t*)&C->rs.epoch;
     const long long iters0 = *(volatile long long*)&C->rs.iters;
     unsigned long long vq_t = vload64(&C->tail[0]), eq_t = vload64(&C->tail[1]), cq_t = vload64(&C->tail[2]);
+    // hub and expansion lists queued in the last wave: between the last two
+    // barrier snapshots (empty at iteration boundaries)
+    auto hubs_pending = [&]() {
+        return vload64(&C->stail[4]) != vload64(&C->sprev[0]) || vload64(&C->stail[5]) != vload64(&C->sprev[1]);
+    };
     LocalStats ls;
     long long iters = 0, rounds = 0, waves = 0, remsum = 0;
     // resume inside the search waves of an iteration the single-block mode began
@@ -235,7 +391,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         int r = 0;
         for (;;) {
             if (r == 0 && fx) {
-                for_each_vertex<MODE>(g, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
+                for_each_vertex<MODE, -1>(g, C, P, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
                 fx = false;
             }
             for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
@@ -333,18 +489,21 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
 
         if (P.op == 0) {
             // -------------------------------------------- SEARCH (insert): frontier + evictions per wave
-            while (fhi > flo || ehi > elo) {
+            while (fhi > flo || ehi > elo || (MODE == 0 && hubs_pending())) {
                 if (MODE == 1 && (fhi - flo) + (ehi - elo) > (unsigned long long)P.big_wave) {
                     escalate = true;   // this wave is too big for one block: hand it to the grid
                     break;
                 }
                 waves++;
-                for_each_vertex<MODE>(g, &C->pc[2], P.VQ, qm, flo, fhi, [&](int v, auto grp) {
-                    process_frontier<decltype(grp)>(g, C, P, v, e, ls);
-                });
-                for_each_vertex<MODE>(g, &C->pc[3], P.EQ, qm, elo, ehi, [&](int v, auto grp) {
-                    evict_insert_vertex<decltype(grp)>(g, C, P, v, e, ls);
-                });
+                for_each_vertex<MODE, HUB_FRONT>(g, C, P, &C->pc[2], P.VQ, qm, flo, fhi,
+                                                 [&](int v, auto grp) {
+                                                     process_frontier<decltype(grp)>(g, C, P, v, e, ls);
+                                                 });
+                for_each_vertex<MODE, HUB_EVICT_INS>(g, C, P, &C->pc[3], P.EQ, qm, elo, ehi,
+                                                     [&](int v, auto grp) {
+                                                         evict_insert_vertex<decltype(grp)>(g, C, P, v, e, ls);
+                                                     });
+                if (MODE == 0) hub_chunks(g, C, P, e, ls);
                 if (!(ok = sync(PH_DISCOVER))) break;
                 flo = fhi;
                 fhi = vload64(&C->stail[0]);
@@ -377,15 +536,17 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             fx_hi = cq_t;
         } else {
             // -------------------------------------------- EVICT (delete); evicted vertices drop by one
-            while (ehi > elo) {
+            while (ehi > elo || (MODE == 0 && hubs_pending())) {
                 if (MODE == 1 && ehi - elo > (unsigned long long)P.big_wave) {
                     escalate = true;
                     break;
                 }
                 waves++;
-                for_each_vertex<MODE>(g, &C->pc[2], P.EQ, qm, elo, ehi, [&](int v, auto grp) {
-                    evict_delete_vertex<decltype(grp)>(g, C, P, v, e, ls);
-                });
+                for_each_vertex<MODE, HUB_EVICT_DEL>(g, C, P, &C->pc[2], P.EQ, qm, elo, ehi,
+                                                     [&](int v, auto grp) {
+                                                         evict_delete_vertex<decltype(grp)>(g, C, P, v, e, ls);
+                                                     });
+                if (MODE == 0) hub_chunks(g, C, P, e, ls);
                 if (!(ok = sync(PH_EVICT))) break;
                 elo = ehi;
                 ehi = vload64(&C->stail[1]);
@@ -420,7 +581,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         }
     }
     if (ok && fx) {
-        for_each_vertex<MODE>(g, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
+        for_each_vertex<MODE, -1>(g, C, P, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
         ok = sync(PH_FIXUP);
     }
     // statistics: one atomic per warp
@@ -468,6 +629,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             __threadfence();
         }
     }
+    if (MODE == 1) loop_control(P, C);   // thread 0 is the leader: its writes above come first
 }
 
 int maintain_blocks_per_sm(int threads) {
@@ -476,10 +638,24 @@ int maintain_blocks_per_sm(int threads) {
     return nb;
 }
 
+// Cooperative (co-resident blocks, which the grid barrier needs); the
+// attribute form also records into a graph under stream capture.
 cudaError_t launch_maintain(const MaintainParams& p, int blocks, int threads, cudaStream_t s) {
-    MaintainParams q = p;
-    void* args[] = {&q};
-    return cudaLaunchCooperativeKernel((const void*)maintain_kernel<0>, dim3(blocks), dim3(threads), args, 0, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, maintain_kernel<0>, p);
+}
+
+const void* maintain_kernel_symbol(int mode) {
+    return mode == 0 ? (const void*)maintain_kernel<0> : (const void*)maintain_kernel<1>;
 }
 
 cudaError_t launch_maintain_block(const MaintainParams& p, int threads, cudaStream_t s) {

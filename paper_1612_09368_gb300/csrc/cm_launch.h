@@ -33,6 +33,11 @@ struct MaintainParams {
     long long small_work;     // ... and the last iteration touched at most this many items
     long long big_work;       // block -> grid mode when an iteration touches more
     long long big_wave;       // block -> grid mode, inside an iteration, before a wave this large
+    HubItem* HQ;              // hub items of the current wave (ring of kHubRing)
+    HubItem* PQ;              // expansion items (ring of kHubRing)
+    int32_t hub_len;          // grid mode: vertices with at least this many slots are scanned grid-wide
+    int32_t use_cond;         // inside a captured step: the single-block kernel drives the loop node
+    unsigned long long cond;  // that node's conditional handle
 };
 
 struct PeelParams {
@@ -48,17 +53,28 @@ struct PeelParams {
     unsigned long long limit_ns;
 };
 
-// ---- maintenance (cm_maintain.cu)
-cudaError_t ingest_a(const int32_t* E, long long k, DevGraph g, BSet* bs, unsigned long long bmask, Ctl* c,
+// ---- maintenance (cm_maintain.cu); kp / np: device item counts of a captured step (else NULL)
+cudaError_t ingest_a(const int32_t* E, long long k, const unsigned long long* kp, DevGraph g, BSet* bs,
+                     unsigned long long bmask, Ctl* c, cudaStream_t s);
+cudaError_t ingest_b(const int32_t* E, long long k, const unsigned long long* kp, int op, DevGraph g,
+                     const BSet* bs, unsigned long long bmask, REdge* R0, int32_t* ovl, Ctl* c, cudaStream_t s);
+cudaError_t index_new_edges(REdge* R, long long n, const unsigned long long* np, DevGraph g, Ctl* c,
+                            cudaStream_t s);
+cudaError_t reloc_size(const int32_t* ovl, long long novl, const unsigned long long* np, DevGraph g, Ctl* c,
+                       cudaStream_t s);
+cudaError_t reloc_gate(DevGraph g, Ctl* c, StepLog* log, int phase, cudaStream_t s);
+cudaError_t relocate(const int32_t* ovl, long long novl, const unsigned long long* np, DevGraph g, Ctl* c,
                      cudaStream_t s);
-cudaError_t ingest_b(const int32_t* E, long long k, int op, DevGraph g, const BSet* bs, unsigned long long bmask,
-                     REdge* R0, int32_t* ovl, Ctl* c, cudaStream_t s);
-cudaError_t reloc_size(const int32_t* ovl, long long novl, DevGraph g, Ctl* c, cudaStream_t s);
-cudaError_t relocate(const int32_t* ovl, long long novl, DevGraph g, Ctl* c, cudaStream_t s);
-cudaError_t clear_need(const REdge* R, long long n, DevGraph g, cudaStream_t s);
+cudaError_t clear_need(const REdge* R, long long n, const unsigned long long* np, DevGraph g, cudaStream_t s);
+cudaError_t step_begin(Ctl* c, StepLog* log, cudaStream_t s);
+cudaError_t phase_begin(Ctl* c, StepLog* log, int phase, cudaStream_t s);
+cudaError_t phase_maintain(Ctl* c, StepLog* log, int phase, cudaStream_t s);
+cudaError_t phase_end(Ctl* c, StepLog* log, int phase, cudaStream_t s);
 cudaError_t apply_structure(const REdge* R, long long n, int op, DevGraph g, Ctl* c, cudaStream_t s);
 cudaError_t launch_maintain(const MaintainParams& p, int blocks, int threads, cudaStream_t s);
 cudaError_t launch_maintain_block(const MaintainParams& p, int threads, cudaStream_t s);
+// kernel symbols of the two execution modes, for graph capture
+const void* maintain_kernel_symbol(int mode);
 int maintain_blocks_per_sm(int threads);
 
 // ---- store / peel (cm_store.cu)
@@ -82,10 +98,12 @@ cudaError_t gather_incident(const int32_t* ids, int32_t count, DevGraph g, int32
 cudaError_t mark_dead(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s);
 cudaError_t export_cores(DevGraph g, int32_t* out, cudaStream_t s);
 cudaError_t export_edges(DevGraph g, int32_t* out, Ctl* c, cudaStream_t s);
-cudaError_t localize_multi(int32_t* E, long long k, const long long* prefix, const int32_t* bases, int32_t ng,
+cudaError_t localize_multi(int32_t* E, long long k, const unsigned long long* kp, const long long* prefix,
+                           const int32_t* bases, int32_t ng, cudaStream_t s);
+cudaError_t validate_pairs(const int32_t* E, long long k, const unsigned long long* kp, int phase, DevGraph g, Ctl* c,
                            cudaStream_t s);
 cudaError_t sum_caps(DevGraph g, int32_t v0, int32_t v1, Ctl* c, cudaStream_t s);
-cudaError_t count_multi(const REdge* R, long long n, const int32_t* bases, int32_t ng, unsigned long long* per_graph,
-                        cudaStream_t s);
+cudaError_t count_multi(const REdge* R, long long n, const unsigned long long* np, const int32_t* bases, int32_t ng,
+                        unsigned long long* per_graph, cudaStream_t s);
 
 }  // namespace cm

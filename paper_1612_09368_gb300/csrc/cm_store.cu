@@ -477,46 +477,72 @@ cudaError_t export_edges(DevGraph g, int32_t* out, Ctl* c, cudaStream_t s) {
 // ------------------------------------------------------------------ multi-graph helpers
 // Local ids of a concatenated per-graph batch -> global ids.  prefix[i] is
 // the first batch entry of graph i (ng+1 entries).
-__global__ void localize_multi_kernel(int32_t* E, long long k, const long long* __restrict__ prefix,
-                                      const int32_t* __restrict__ bases, int32_t ng) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k) return;
-    int lo = 0, hi = ng - 1;
-    while (lo < hi) {                 // last graph whose prefix <= i
-        int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= i) lo = mid; else hi = mid - 1;
+__global__ void localize_multi_kernel(int32_t* E, long long k, const unsigned long long* kp,
+                                      const long long* __restrict__ prefix, const int32_t* __restrict__ bases,
+                                      int32_t ng) {
+    if (kp) k = (long long)vload64(kp);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int lo = 0, hi = ng - 1;
+        while (lo < hi) {                 // last graph whose prefix <= i
+            int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        int b = bases[lo];
+        int nv = bases[lo + 1] - b;       // bases has ng+1 entries
+        int32_t u = E[2 * i], v = E[2 * i + 1];
+        // an id outside its graph stays invalid (negative) so ingest rejects it
+        E[2 * i] = (u >= 0 && u < nv) ? u + b : -1;
+        E[2 * i + 1] = (v >= 0 && v < nv) ? v + b : -1;
     }
-    int b = bases[lo];
-    int nv = bases[lo + 1] - b;       // bases has ng+1 entries
-    int32_t u = E[2 * i], v = E[2 * i + 1];
-    // an id outside its graph stays invalid (negative) so ingest rejects it
-    E[2 * i] = (u >= 0 && u < nv) ? u + b : -1;
-    E[2 * i + 1] = (v >= 0 && v < nv) ? v + b : -1;
 }
 
-__global__ void count_multi_kernel(const REdge* __restrict__ R, long long n, const int32_t* __restrict__ bases,
-                                   int32_t ng, unsigned long long* per_graph) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int x = R[i].lo;
-    int lo = 0, hi = ng - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (bases[mid] <= x) lo = mid; else hi = mid - 1;
+__global__ void count_multi_kernel(const REdge* __restrict__ R, long long n, const unsigned long long* np,
+                                   const int32_t* __restrict__ bases, int32_t ng, unsigned long long* per_graph) {
+    if (np) n = (long long)vload64(np);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int x = R[i].lo;
+        int lo = 0, hi = ng - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (bases[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        atomicAdd(&per_graph[lo], 1ull);
     }
-    atomicAdd(&per_graph[lo], 1ull);
 }
 
-cudaError_t localize_multi(int32_t* E, long long k, const long long* prefix, const int32_t* bases, int32_t ng,
-                           cudaStream_t s) {
+// Captured step: every id of a batch names a live vertex (checked for both
+// batches before anything changes).  bad_index gets (phase << 40) | i.
+__global__ void validate_pairs_kernel(const int32_t* __restrict__ E, long long k, const unsigned long long* kp,
+                                      int phase, DevGraph g, Ctl* c) {
+    if (kp) k = (long long)vload64(kp);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t u = E[2 * i], v = E[2 * i + 1];
+        if (u < 0 || v < 0 || u >= g.n || v >= g.n || g.hs[u].x < 0 || g.hs[v].x < 0) {
+            atomicMin(&c->bad_index, ((long long)phase << 40) | i);
+            atomicCAS(&c->error, 0, E_INVALID);
+        }
+    }
+}
+
+cudaError_t localize_multi(int32_t* E, long long k, const unsigned long long* kp, const long long* prefix,
+                           const int32_t* bases, int32_t ng, cudaStream_t s) {
     if (k <= 0) return cudaSuccess;
-    localize_multi_kernel<<<grid_for(k, 256, 1ll << 31), 256, 0, s>>>(E, k, prefix, bases, ng);
+    localize_multi_kernel<<<grid_for(k, 256, 8192), 256, 0, s>>>(E, k, kp, prefix, bases, ng);
     return cudaGetLastError();
 }
-cudaError_t count_multi(const REdge* R, long long n, const int32_t* bases, int32_t ng, unsigned long long* per_graph,
-                        cudaStream_t s) {
+cudaError_t count_multi(const REdge* R, long long n, const unsigned long long* np, const int32_t* bases, int32_t ng,
+                        unsigned long long* per_graph, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    count_multi_kernel<<<grid_for(n, 256, 1ll << 31), 256, 0, s>>>(R, n, bases, ng, per_graph);
+    count_multi_kernel<<<grid_for(n, 256, 8192), 256, 0, s>>>(R, n, np, bases, ng, per_graph);
+    return cudaGetLastError();
+}
+cudaError_t validate_pairs(const int32_t* E, long long k, const unsigned long long* kp, int phase, DevGraph g, Ctl* c,
+                           cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    validate_pairs_kernel<<<grid_for(k, 256, 8192), 256, 0, s>>>(E, k, kp, phase, g, c);
     return cudaGetLastError();
 }
 

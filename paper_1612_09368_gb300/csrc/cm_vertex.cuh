@@ -107,78 +107,64 @@ __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, i
     w[3] = t0 + 3 < len ? a.w : HOLE;
 }
 
-#define SCAN4_BEGIN(Grp, len)                                                   \
-    for (int base_ = Grp::first() * 4; base_ < (len); base_ += Grp::G * 4) {     \
+// Slots [s0, s1) of a list (s0 a multiple of 4), four per thread per step.
+#define SCAN4_RANGE(Grp, s0, s1)                                                      \
+    for (int base_ = (s0) + Grp::first() * 4; base_ < (s1); base_ += Grp::G * 4) {     \
         const int t0_ = base_ + lane_id() * 4;
+#define SCAN4_BEGIN(Grp, len) SCAN4_RANGE(Grp, 0, len)
 #define SCAN4_END }
 
-// ---------------------------------------------------------------- per-vertex phase bodies
-// Positive search step (Algorithm 3) for a frontier vertex v at level k:
-// support += CSD(v); above k -> visit the unvisited core-k neighbours with
-// SD > k, else v is evicted.
+// ---------------------------------------------------------------- range scans
+// Each scan covers slots [s0, s1) of the list at offset o of a vertex at
+// level k, so a vertex can be scanned whole by one group or in chunks by
+// many blocks.
+
+// This thread's part of CSD over the range (Definition 8 with the SD of
+// Definition 7: neighbours above k, and core-k neighbours with SD > k).
 template <class Grp>
-__device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                 uint32_t e, LocalStats& ls) {
-    const int lane = lane_id();
-    const int k = g.hs[v].x;
-    const long long o = g.off[v];
-    const int len = g.end[v];
+__device__ __forceinline__ int csd_part(const DevGraph& g, int k, long long o, int s0, int s1) {
     int pcd = 0;
-    SCAN4_BEGIN(Grp, len)
+    SCAN4_RANGE(Grp, s0, s1)
         int w[4];
-        load4(g, o, len, t0_, w);
+        load4(g, o, s1, t0_, w);
         int2 h[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? *reinterpret_cast<const int2*>(&g.hs[w[q]]) : make_int2(-1, 0);
 #pragma unroll
         for (int q = 0; q < 4; q++) pcd += (h[q].x > k) || (h[q].x == k && h[q].y > k);
     SCAN4_END
-    pcd = Grp::sum(pcd);
-    int32_t sup = 0;
-    if (Grp::rank0()) {
-        uint32_t of;
-        int32_t oc;
-        add_word(g, C, v, e, pcd, kProcessed, of, oc);
-        sup = oc + pcd;
-        ls.vis++;
-        ls.visl += len;
-    }
-    if constexpr (Grp::G == 32) {
-        sup = __shfl_sync(0xffffffffu, sup, 0);
-    } else {
-        sup = Grp::sum(Grp::rank0() ? sup : 0);
-    }
-    if (sup > k) {
-        SCAN4_BEGIN(Grp, len)
-            int w[4];
-            load4(g, o, len, t0_, w);
-            int4 h[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
-                bool p = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e);
-                warp_push(&C->tail[0], P.VQ, P.qmask, p, w[q]);
-            }
-        SCAN4_END
-    } else if (Grp::warp0()) {
-        warp_push(&C->tail[1], P.EQ, P.qmask, lane == 0, v);
-    }
+    return pcd;
 }
 
-// InsertRemove step (Algorithm 4): v leaves; every core-k neighbour with
+// Visits the unvisited core-k neighbours with SD > k in the range and
+// appends them to the next frontier.
+template <class Grp>
+__device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k, long long o,
+                                             int s0, int s1, uint32_t e) {
+    SCAN4_RANGE(Grp, s0, s1)
+        int w[4];
+        load4(g, o, s1, t0_, w);
+        int4 h[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
+            bool p = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e);
+            warp_push(&C->tail[0], P.VQ, P.qmask, p, w[q]);
+        }
+    SCAN4_END
+}
+
+// InsertRemove over the range (Algorithm 4): every core-k neighbour with
 // SD > k (visited or not) loses one support; a processed one whose support
 // falls to k leaves too.
 template <class Grp>
-__device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                    uint32_t e, LocalStats& ls) {
-    const int k = g.hs[v].x;
-    const long long o = g.off[v];
-    const int len = g.end[v];
-    SCAN4_BEGIN(Grp, len)
+__device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
+                                                long long o, int s0, int s1, uint32_t e) {
+    SCAN4_RANGE(Grp, s0, s1)
         int w[4];
-        load4(g, o, len, t0_, w);
+        load4(g, o, s1, t0_, w);
         int4 h[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
@@ -195,24 +181,17 @@ __device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, c
             warp_push(&C->tail[1], P.EQ, P.qmask, p, w[q]);
         }
     SCAN4_END
-    if (Grp::rank0()) {
-        ls.ev++;
-        ls.evl += len;
-    }
 }
 
-// DeleteRemove step (Algorithm 7): v drops to k-1; each core-k neighbour w
-// loses one support (initially SD(w)) and leaves when it falls below k,
-// i.e. when its count of evicted neighbours reaches SD(w) - k + 1.
+// DeleteRemove over the range (Algorithm 7): each core-k neighbour w loses
+// one support (initially SD(w)) and leaves when it falls below k, i.e. when
+// its count of evicted neighbours reaches SD(w) - k + 1.
 template <class Grp>
-__device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                    uint32_t e, LocalStats& ls) {
-    const int k = g.hs[v].x;
-    const long long o = g.off[v];
-    const int len = g.end[v];
-    SCAN4_BEGIN(Grp, len)
+__device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
+                                                long long o, int s0, int s1, uint32_t e) {
+    SCAN4_RANGE(Grp, s0, s1)
         int w[4];
-        load4(g, o, len, t0_, w);
+        load4(g, o, s1, t0_, w);
         int4 h[4];
         uint32_t c[4];
 #pragma unroll
@@ -237,6 +216,60 @@ __device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, c
             warp_push(&C->tail[1], P.EQ, P.qmask, p, w[q]);
         }
     SCAN4_END
+}
+
+// ---------------------------------------------------------------- per-vertex phase bodies
+// Positive search step (Algorithm 3) for a frontier vertex v at level k:
+// support += CSD(v); above k -> visit the unvisited core-k neighbours with
+// SD > k, else v is evicted.
+template <class Grp>
+__device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                 uint32_t e, LocalStats& ls) {
+    const int lane = lane_id();
+    const int k = g.hs[v].x;
+    const long long o = g.off[v];
+    const int len = g.end[v];
+    const int pcd = Grp::sum(csd_part<Grp>(g, k, o, 0, len));
+    int32_t sup = 0;
+    if (Grp::rank0()) {
+        uint32_t of;
+        int32_t oc;
+        add_word(g, C, v, e, pcd, kProcessed, of, oc);
+        sup = oc + pcd;
+        ls.vis++;
+        ls.visl += len;
+    }
+    if constexpr (Grp::G == 32) {
+        sup = __shfl_sync(0xffffffffu, sup, 0);
+    } else {
+        sup = Grp::sum(Grp::rank0() ? sup : 0);
+    }
+    if (sup > k) {
+        expand_range<Grp>(g, C, P, k, o, 0, len, e);
+    } else if (Grp::warp0()) {
+        warp_push(&C->tail[1], P.EQ, P.qmask, lane == 0, v);
+    }
+}
+
+// InsertRemove step (Algorithm 4) for an evicted vertex v.
+template <class Grp>
+__device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                    uint32_t e, LocalStats& ls) {
+    const int len = g.end[v];
+    evict_ins_range<Grp>(g, C, P, g.hs[v].x, g.off[v], 0, len, e);
+    if (Grp::rank0()) {
+        ls.ev++;
+        ls.evl += len;
+    }
+}
+
+// DeleteRemove step (Algorithm 7) for an evicted vertex v, which drops to k-1.
+template <class Grp>
+__device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
+                                                    uint32_t e, LocalStats& ls) {
+    const int k = g.hs[v].x;
+    const int len = g.end[v];
+    evict_del_range<Grp>(g, C, P, k, g.off[v], 0, len, e);
     if constexpr (Grp::G > 32) __syncthreads();   // every warp has read k before it changes
     if (Grp::rank0()) {
         g.hs[v].x = k - 1;

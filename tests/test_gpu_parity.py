@@ -274,6 +274,44 @@ def test_hub_overflow_relocation(cm):
     assert set(map(tuple, got.tolist())) == set(map(tuple, exp.tolist()))
 
 
+@pytest.mark.parametrize("grid_only", [True, False])
+def test_hub_chunked_scans(cm, grid_only):
+    """Vertices with at least hub_slots slots are scanned by every block in
+    chunks of 2048 slots (frontier sums, expansion, both evictions); with a
+    low threshold most of an R-MAT graph's upper shells take that path, and
+    its largest lists span several chunks."""
+    scale = 14
+    n = 1 << scale
+    e = synth.rmat(scale, 16, synth.stream(40))
+    rng = np.random.default_rng(40)
+    stars = [np.stack([np.full(5000, h), rng.choice(n, 5000, replace=False)], 1) for h in (5, 77, 901)]
+    e = np.concatenate([e] + stars).astype(np.int32)
+    e = np.unique(np.sort(e, 1), axis=0)
+    e = e[e[:, 0] != e[:, 1]]
+    opts = {"hub_slots": 256}
+    if grid_only:
+        opts["block_mode_edges"] = -1
+    g = cm.CoreGraph(n, _dev(e), **opts)
+    ref = oracle.OracleGraph(n, e, mode=oracle.SUPERIOR)
+    deg = np.bincount(e.ravel(), minlength=n)
+    assert deg.max() > 2 * 2048
+    cur = e
+    for b, (op, law, k) in enumerate([(0, synth.UNIFORM, 3000), (0, synth.PREFERENTIAL, 3000),
+                                      (1, synth.PREFERENTIAL, 4000), (1, synth.UNIFORM, 4000),
+                                      (0, synth.PREFERENTIAL, 20000), (1, synth.PREFERENTIAL, 20000)]):
+        if op == 0:
+            batch = synth.static_sample_insert(n, cur, k, law, synth.stream(41, 0, b))
+            got, exp = g.insert_edges(_dev(batch)), ref.insert_edges(batch)
+        else:
+            batch = synth.static_sample_delete(n, cur, k, law, synth.stream(42, 0, b), synth.csr(n, cur))
+            got, exp = g.delete_edges(_dev(batch)), ref.delete_edges(batch)
+        assert got == exp
+        assert g.stats()["iterations"] == ref.last_iterations(), b
+        _check_same(g, ref, f"batch {b}")
+        cur = ref.edges()
+    assert (g.cores() == oracle.bz(n, cur)).all()
+
+
 def test_structure_apply_then_repeel(cm):
     """The full re-peel comparator: apply the batch to the structure only,
     then recompute every core by GPU peeling."""
