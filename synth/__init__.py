@@ -56,6 +56,8 @@ def _L():
                 "sy_er": (i64, [i32, i64, u64, _i32p]),
                 "sy_rmat": (i64, [i32, i64, dbl, dbl, dbl, u64, i32, _i32p]),
                 "sy_ba": (i64, [i32, i32, u64, _i32p]),
+                "sy_ba_many": (ctypes.c_int, [i32, _i32p, _i32p, vp, _i64p, _i32p, i32, _i64p, _i64p, vp, _i64p,
+                                              _i64p, _i32p, _i32p]),
                 "sy_grid": (i64, [i32, i64, u64, _i32p]),
                 "sy_dyn_create": (vp, [i32, i64, _i32p]),
                 "sy_dyn_free": (None, [vp]),
@@ -131,6 +133,45 @@ def ba(n: int, m: int, seed: int) -> np.ndarray:
     if got != cnt:
         raise ValueError(f"sy_ba failed ({got})")
     return out
+
+
+def ba_edge_count(n: int, m: int) -> int:
+    """Edges of ba(n, m): a clique on m + 1 vertices, then m per vertex."""
+    return m * (m + 1) // 2 + (n - m - 1) * m
+
+
+def ba_many(ns, ms, gseeds, kins, kdel, bseeds):
+    """Many BA graphs and per-graph batches (see sy_ba_many).  kins, kdel,
+    bseeds: arrays [rounds, ngraphs].  Returns (edges [sum m, 2] in graph
+    order with local ids, eoff [ng+1], ins [rounds] list of arrays, del
+    [rounds] list of arrays), round r's arrays holding every graph's batch
+    in graph order."""
+    ns = np.ascontiguousarray(ns, dtype=np.int32)
+    ms = np.ascontiguousarray(ms, dtype=np.int32)
+    ng = len(ns)
+    kins = np.ascontiguousarray(kins, dtype=np.int64).reshape(-1, ng)
+    kdel = np.ascontiguousarray(kdel, dtype=np.int64).reshape(-1, ng)
+    rounds = kins.shape[0]
+    gs = np.ascontiguousarray(gseeds, dtype=np.uint64)
+    bs = np.ascontiguousarray(bseeds, dtype=np.uint64).reshape(-1)
+    ecount = np.array([ba_edge_count(int(n), int(m)) for n, m in zip(ns, ms)], dtype=np.int64)
+    eoff = np.zeros(ng + 1, dtype=np.int64)
+    eoff[1:] = np.cumsum(ecount)
+    ioff = np.zeros(rounds * ng + 1, dtype=np.int64)
+    ioff[1:] = np.cumsum(kins.reshape(-1))
+    doff = np.zeros(rounds * ng + 1, dtype=np.int64)
+    doff[1:] = np.cumsum(kdel.reshape(-1))
+    edges = np.empty((int(eoff[-1]), 2), dtype=np.int32)
+    ins = np.empty((int(ioff[-1]), 2), dtype=np.int32)
+    dele = np.empty((int(doff[-1]), 2), dtype=np.int32)
+    rc = _L().sy_ba_many(ng, _p32(ns), _p32(ms), gs.ctypes.data, eoff.ctypes.data_as(_i64p), _p32(edges), rounds,
+                         kins.ctypes.data_as(_i64p), kdel.ctypes.data_as(_i64p), bs.ctypes.data,
+                         ioff.ctypes.data_as(_i64p), doff.ctypes.data_as(_i64p), _p32(ins), _p32(dele))
+    if rc != 0:
+        raise RuntimeError(f"sy_ba_many failed ({rc})")
+    ins_r = [ins[ioff[r * ng]: ioff[(r + 1) * ng]] for r in range(rounds)]
+    del_r = [dele[doff[r * ng]: doff[(r + 1) * ng]] for r in range(rounds)]
+    return edges, eoff, ins_r, del_r
 
 
 def grid(side: int, nshort: int, seed: int) -> np.ndarray:

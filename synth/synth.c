@@ -591,3 +591,80 @@ int sy_csr(int32_t n, int64_t m, const int32_t* edges, int64_t* row_off, int32_t
     free(fill);
     return 0;
 }
+
+/* ---------------- many Barabasi-Albert graphs with per-graph batches ----------------
+ * Graph i (n = ns[i], attachment m = ms[i], seed gseeds[i]) is written at
+ * edges + 2*eoff[i].  For round r and graph i (slot j = r*ng + i, so each
+ * round's batches are contiguous in graph order) kins[j] distinct uniform
+ * pairs absent from the generated graph go to ins + 2*ioff[j] and kdel[j]
+ * distinct uniform edges of it to del + 2*doff[j] (seed bseeds[j]).  Every
+ * round is drawn against the graph as generated.  Graphs run in parallel.
+ * Returns 0, or -1 (bad arguments), -2 (memory), -3 (a batch could not be
+ * filled). */
+int sy_ba_many(int32_t ng, const int32_t* ns, const int32_t* ms, const uint64_t* gseeds, const int64_t* eoff,
+               int32_t* edges, int32_t rounds, const int64_t* kins, const int64_t* kdel, const uint64_t* bseeds,
+               const int64_t* ioff, const int64_t* doff, int32_t* ins, int32_t* del) {
+    int status = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t i = 0; i < ng; i++) {
+        int32_t* e = edges + 2 * eoff[i];
+        int64_t m = sy_ba(ns[i], ms[i], gseeds[i], e);
+        if (m != eoff[i + 1] - eoff[i]) {
+#pragma omp atomic write
+            status = -1;
+            continue;
+        }
+        uint64_t* keys = (uint64_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(uint64_t));
+        if (!keys) {
+#pragma omp atomic write
+            status = -2;
+            continue;
+        }
+        for (int64_t q = 0; q < m; q++) keys[q] = ekey(e[2 * q], e[2 * q + 1]);
+        if (radix_sort_u64(keys, m)) {
+            free(keys);
+#pragma omp atomic write
+            status = -2;
+            continue;
+        }
+        for (int32_t r = 0; r < rounds; r++) {
+            const int64_t j = (int64_t)r * ng + i;
+            rng_t g = {bseeds[j], 0};
+            hmap b;
+            if (hm_init(&b, kins[j] + kdel[j])) {
+#pragma omp atomic write
+                status = -2;
+                break;
+            }
+            int32_t* oi = ins + 2 * ioff[j];
+            int64_t got = 0, tries = 0, lim = 64 * kins[j] + 1024;
+            while (got < kins[j] && tries++ < lim) {
+                int32_t u = (int32_t)below(rnext(&g), (uint64_t)ns[i]);
+                int32_t v = (int32_t)below(rnext(&g), (uint64_t)ns[i]);
+                if (u == v) continue;
+                uint64_t k = ekey(u, v);
+                if (key_present(keys, m, k)) continue;
+                if (hm_put(&b, k, got)) { oi[2 * got] = u; oi[2 * got + 1] = v; got++; }
+            }
+            int32_t* od = del + 2 * doff[j];
+            int64_t gd = 0;
+            tries = 0;
+            lim = 64 * kdel[j] + 1024;
+            while (gd < kdel[j] && m > 0 && tries++ < lim) {
+                int64_t q = (int64_t)below(rnext(&g), (uint64_t)m);
+                if (hm_put(&b, ~ekey(e[2 * q], e[2 * q + 1]), gd)) {   /* own key space: never an insert key */
+                    od[2 * gd] = e[2 * q];
+                    od[2 * gd + 1] = e[2 * q + 1];
+                    gd++;
+                }
+            }
+            hm_free(&b);
+            if (got < kins[j] || gd < kdel[j]) {
+#pragma omp atomic write
+                status = -3;
+            }
+        }
+        free(keys);
+    }
+    return status;
+}

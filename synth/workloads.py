@@ -15,6 +15,7 @@ import numpy as np
 
 from . import (DELETE, GRAPH, INSERT, PREFERENTIAL, UNIFORM, VDELETE, VINSERT, DynGraph, ba, er, rmat, stream,
                uniform)
+from . import ba_many as _ba_many
 
 EDGE_UNIFORM = PREFERENTIAL   # "a uniform random existing edge" is the degree-proportional delete law
 
@@ -105,22 +106,31 @@ def rmat_sweep(scale: int = 24, edge_factor: int = 16, sizes=(10 ** 3, 10 ** 4, 
     return n, e, batches
 
 
-def ba_many(ngraphs: int = 512, cfg: int = 4, nmin_exp: float = 3.0, nmax_exp: float = 6.0):
-    """Barabasi-Albert graphs with n log-uniform in [10^nmin_exp, 10^nmax_exp]
-    and m uniform in {4..16}; per graph a batch of size log-uniform in
-    [10, 10^4]: 70% uniform new edges, then 30% uniform existing edges."""
-    out = []
+def ba_many(ngraphs: int = 512, rounds: int = 1, cfg: int = 4, nmin_exp: float = 3.0, nmax_exp: float = 6.0,
+            bmin_exp: float = 1.0, bmax_exp: float = 4.0, frac_insert: float = 0.7):
+    """Barabasi-Albert graphs with n log-uniform in [10^nmin_exp,
+    10^nmax_exp] and attachment m uniform in {4..16}; per graph and round a
+    batch of size log-uniform in [10^bmin_exp, 10^bmax_exp], 70% new
+    uniform pairs and 30% uniform existing edges, every round drawn against
+    the graph as generated (a round is applied, timed, then undone).
+    Returns dict(ns, ms, edges, eoff, ins [rounds], dele [rounds],
+    kins [rounds, ng], kdel [rounds, ng])."""
+    ns = np.empty(ngraphs, dtype=np.int32)
+    ms = np.empty(ngraphs, dtype=np.int32)
+    gseeds = np.empty(ngraphs, dtype=np.uint64)
+    kins = np.empty((rounds, ngraphs), dtype=np.int64)
+    kdel = np.empty((rounds, ngraphs), dtype=np.int64)
+    bseeds = np.empty((rounds, ngraphs), dtype=np.uint64)
     for gi in range(ngraphs):
         s = stream(cfg, gi, 0, 5)   # parameters
-        n = int(10 ** (nmin_exp + (nmax_exp - nmin_exp) * uniform(s, 0)))
-        m = 4 + int(13 * uniform(s, 1))
-        b = int(10 ** (1 + 3 * uniform(s, 2)))
-        e = ba(n, m, stream(cfg, gi, 0, GRAPH))
-        d = DynGraph(n, e)
-        k_ins = int(round(0.7 * b))
-        a = d.sample_insert(k_ins, UNIFORM, stream(cfg, gi, 0, INSERT))
-        d.apply(0, a)
-        dl = d.sample_delete(b - k_ins, EDGE_UNIFORM, stream(cfg, gi, 0, DELETE))
-        d.apply(1, dl)
-        out.append({"n": n, "m": m, "edges": e, "ins": a, "dele": dl, "final": d})
-    return out
+        ns[gi] = int(10 ** (nmin_exp + (nmax_exp - nmin_exp) * uniform(s, 0)))
+        ms[gi] = 4 + int(13 * uniform(s, 1))
+        gseeds[gi] = stream(cfg, gi, 0, GRAPH)
+        for r in range(rounds):
+            sb = stream(cfg, gi, r + 1, 5)
+            b = int(10 ** (bmin_exp + (bmax_exp - bmin_exp) * uniform(sb, 0)))
+            kins[r, gi] = int(round(frac_insert * b))
+            kdel[r, gi] = b - kins[r, gi]
+            bseeds[r, gi] = stream(cfg, gi, r + 1, INSERT)
+    edges, eoff, ins, dele = _ba_many(ns, ms, gseeds, kins, kdel, bseeds)
+    return {"ns": ns, "ms": ms, "edges": edges, "eoff": eoff, "ins": ins, "dele": dele, "kins": kins, "kdel": kdel}

@@ -53,3 +53,31 @@ def test_dyn_streams():
     dead = d.delete_vertices(3, synth.stream(5, 0, 0, synth.VDELETE))
     al = d.alive()
     assert (~al[dead]).all() and all(d.degree(int(v)) == 0 for v in dead)
+
+
+def test_ba_many_graphs_and_batches():
+    """Each generated graph equals the single-graph BA generator with its
+    seed; each round's inserts are distinct pairs absent from its graph and
+    its deletes distinct edges of it, laid out round by round in graph
+    order."""
+    from synth import workloads
+    w = workloads.ba_many(12, rounds=2, nmax_exp=3.6)
+    ns, ms, e, eoff = w["ns"], w["ms"], w["edges"], w["eoff"]
+    assert ((ms >= 4) & (ms <= 16)).all() and ((ns >= 1000) & (ns < 10 ** 3.6)).all()
+    for r in range(2):
+        io = do = 0
+        for i in range(12):
+            g = e[eoff[i]:eoff[i + 1]]
+            if r == 0:
+                assert (g == synth.ba(int(ns[i]), int(ms[i]), synth.stream(4, i, 0, synth.GRAPH))).all()
+            ki, kd = int(w["kins"][r, i]), int(w["kdel"][r, i])
+            assert 10 <= ki + kd <= 10 ** 4 and abs(ki - 0.7 * (ki + kd)) <= 1
+            E = set(map(tuple, np.sort(g, 1).tolist()))
+            a = set(map(tuple, np.sort(w["ins"][r][io:io + ki], 1).tolist()))
+            d = set(map(tuple, np.sort(w["dele"][r][do:do + kd], 1).tolist()))
+            assert len(a) == ki and len(d) == kd
+            assert not (a & E) and d <= E
+            assert all(u != v and 0 <= u < ns[i] and 0 <= v < ns[i] for u, v in a)
+            io += ki
+            do += kd
+        assert io == len(w["ins"][r]) and do == len(w["dele"][r])
