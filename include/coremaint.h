@@ -301,6 +301,72 @@ int cm_step_autotune(cm_step* s, const int64_t* ins_counts, const int32_t* ins_e
 
 void cm_step_destroy(cm_step* s);
 
+/* ---------------- serving: resident graphs, continuous batching ----------------
+ * Not in the paper: a request loop over graphs kept on the device.  Each
+ * graph gets an equal slice of `device_budget_bytes`, split into a ring of
+ * staged insert batches and a ring of staged delete batches: a request is
+ * admitted (its edges copied to the device on a stream of its own, while
+ * the graph's current call runs) once its ring has contiguous room, in
+ * arrival order.  The graph's worker thread then takes the oldest admitted
+ * requests as one round: the longest run, in arrival order, whose inserted
+ * edges and deleted edges are disjoint, at most max_round_edges edges (<= 0:
+ * no limit).  Applying all of its inserts and then all of its deletes is then
+ * exactly applying the requests one by one, and a round is ONE update step
+ * (cm_step: both batches in one CUDA graph replay; two plain calls on a
+ * handle that runs on the legacy default stream).  Graphs are served by
+ * separate threads, so their calls overlap on the device when the handles
+ * run on separate created streams; give each handle a share of the SMs
+ * (cm_options.max_sms) to let the grid-wide launches of different graphs run
+ * side by side.  Each graph ends in the state of applying its requests one
+ * by one, whatever the timing or the other graphs' traffic.  A request that
+ * names an invalid vertex fails alone (its round is replayed request by
+ * request).  Besides the budget, each graph holds one captured step sized
+ * for min(slice / 16 bytes, max_round_edges) edges per operation.  The
+ * server does not own the handles; while it runs, touch them only through
+ * it.  Requests use local ids and host buffers (copied at submit). */
+typedef struct cm_server cm_server;
+
+typedef struct cm_request_result {
+    int32_t status;          /* CM_OK or the error of the request's round */
+    int32_t pad;
+    int64_t round;           /* server-wide round number that applied it */
+    int64_t round_applied;   /* edges the round applied (all its requests together) */
+    int64_t round_edges;     /* edges the round was given */
+    int64_t round_requests;  /* requests merged into the round */
+    int64_t latency_ns;      /* submit -> end of its round */
+    int64_t queue_ns;        /* submit -> admitted (on the device) */
+} cm_request_result;
+
+typedef struct cm_server_stats {
+    int64_t submitted, completed, rounds, coalesced, failed, edges;
+    int64_t p50_ns, p99_ns;  /* over completed requests, submit -> done */
+    int64_t reserved[4];
+} cm_server_stats;
+
+/* Errors: CM_ERR_INVALID (bad arguments, budget below 16 bytes per graph), CM_ERR_OOM. */
+int cm_server_create(cm_server** out, cm_graph* const* graphs, int32_t ngraphs, int64_t device_budget_bytes,
+                     int64_t max_round_edges);
+/* Queues a batch of k edges for graph `graph`; returns at once.  Errors:
+ * CM_ERR_INVALID, CM_ERR_CAPACITY (k above the graph's ring for that operation, slice / 16 bytes:
+ * it could never be admitted). */
+int cm_server_submit(cm_server* s, int32_t graph, int32_t op, const int32_t* edges, int64_t k, int64_t* request_id);
+/* Blocks until the request's round finished; returns the round's status. */
+int cm_server_wait(cm_server* s, int64_t request_id, cm_request_result* out);
+/* Blocks until every submitted request finished (CM_ERR_STATE if any failed). */
+int cm_server_drain(cm_server* s);
+/* Core numbers of a resident graph between two of its rounds (host or device out). */
+int cm_server_get_cores(cm_server* s, int32_t graph, int32_t* out);
+int cm_server_get_stats(cm_server* s, cm_server_stats* out);
+/* Open-loop trace: request i (graph[i], op[i], counts[i] edges, edges
+ * concatenated) is submitted at arrival_ns[i] after the call starts, by a
+ * driver thread, whether or not earlier requests finished.  latency_ns[i]
+ * (nullable) = end of its round - its scheduled arrival; round_of[i]
+ * (nullable) = its round; wall_s = start -> last completion. */
+int cm_server_run_trace(cm_server* s, int64_t nreq, const int64_t* arrival_ns, const int32_t* graph,
+                        const int32_t* op, const int64_t* counts, const int32_t* edges, int64_t* latency_ns,
+                        int64_t* round_of, double* wall_s);
+void cm_server_destroy(cm_server* s);
+
 /* ---------------- decomposition without device allocation ----------------
  * The paper has no counterpart of this entry point; it serves callers that
  * cannot call cudaMalloc -- a process whose framework already reserved the

@@ -84,6 +84,23 @@ class cm_tune_report(ctypes.Structure):
                 ("tried", ctypes.c_int32), ("reps", ctypes.c_int32)]
 
 
+class cm_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("pad", ctypes.c_int32)] + [
+        (k, ctypes.c_int64) for k in ("round", "round_applied", "round_edges", "round_requests", "latency_ns",
+                                      "queue_ns")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class cm_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "rounds", "coalesced", "failed", "edges",
+                                              "p50_ns", "p99_ns")] + [("reserved", ctypes.c_int64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class CoreMaintError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{msg} (code {code})")
@@ -135,6 +152,15 @@ def lib():
             "cm_step_counters": (ctypes.c_int, [vp, p64, p64, p64]),
             "cm_step_autotune": (ctypes.c_int, [vp, p64, vp, p64, vp, i32, ctypes.POINTER(cm_tune_report)]),
             "cm_step_destroy": (None, [vp]),
+            "cm_server_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i64, i64]),
+            "cm_server_submit": (ctypes.c_int, [vp, i32, i32, vp, i64, p64]),
+            "cm_server_wait": (ctypes.c_int, [vp, i64, ctypes.POINTER(cm_request_result)]),
+            "cm_server_drain": (ctypes.c_int, [vp]),
+            "cm_server_get_cores": (ctypes.c_int, [vp, i32, vp]),
+            "cm_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(cm_server_stats)]),
+            "cm_server_run_trace": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp, vp, vp,
+                                                   ctypes.POINTER(ctypes.c_double)]),
+            "cm_server_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -554,3 +580,84 @@ class Step:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Request loop over resident graphs (see cm_server_create): update
+    batches are admitted into each graph's slice of a device budget as
+    room frees up, consecutive same-operation requests are coalesced into
+    one maintenance call, and graphs are served concurrently."""
+
+    def __init__(self, graphs, device_budget_bytes: int, max_round_edges: int = 0):
+        self.graphs = list(graphs)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle.value for g in self.graphs])
+        self._s = ctypes.c_void_p()
+        rc = lib().cm_server_create(ctypes.byref(self._s), arr, len(self.graphs), int(device_budget_bytes),
+                                    int(max_round_edges))
+        if rc != CM_OK:
+            raise CoreMaintError(rc, "cm_server_create")
+
+    def submit(self, graph: int, op: int, edges) -> int:
+        e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        rid = ctypes.c_int64(0)
+        rc = lib().cm_server_submit(self._s, int(graph), int(op), ctypes.c_void_p(e.ctypes.data), len(e),
+                                    ctypes.byref(rid))
+        if rc != CM_OK:
+            raise CoreMaintError(rc, "cm_server_submit")
+        return rid.value
+
+    def wait(self, request_id: int) -> dict:
+        r = cm_request_result()
+        lib().cm_server_wait(self._s, int(request_id), ctypes.byref(r))
+        return r.as_dict()
+
+    def drain(self) -> int:
+        return int(lib().cm_server_drain(self._s))
+
+    def cores(self, graph: int) -> np.ndarray:
+        out = np.empty(cm_num_vertices(self.graphs[graph].handle), dtype=np.int32)
+        rc = lib().cm_server_get_cores(self._s, int(graph), ctypes.c_void_p(out.ctypes.data))
+        if rc != CM_OK:
+            raise CoreMaintError(rc, "cm_server_get_cores")
+        return out
+
+    def stats(self) -> dict:
+        st = cm_server_stats()
+        lib().cm_server_get_stats(self._s, ctypes.byref(st))
+        return st.as_dict()
+
+    def run_trace(self, arrival_ns, graph, op, counts, edges):
+        """Open-loop replay; returns (latency_ns, round_of, wall_s)."""
+        a = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        gr = np.ascontiguousarray(graph, dtype=np.int32)
+        o = np.ascontiguousarray(op, dtype=np.int32)
+        c = np.ascontiguousarray(counts, dtype=np.int64)
+        e = np.ascontiguousarray(edges, dtype=np.int32)
+        lat = np.zeros(len(a), dtype=np.int64)
+        rnd = np.zeros(len(a), dtype=np.int64)
+        wall = ctypes.c_double(0)
+        rc = lib().cm_server_run_trace(self._s, len(a), ctypes.c_void_p(a.ctypes.data),
+                                       ctypes.c_void_p(gr.ctypes.data), ctypes.c_void_p(o.ctypes.data),
+                                       ctypes.c_void_p(c.ctypes.data), ctypes.c_void_p(e.ctypes.data),
+                                       ctypes.c_void_p(lat.ctypes.data), ctypes.c_void_p(rnd.ctypes.data),
+                                       ctypes.byref(wall))
+        if rc != CM_OK:
+            raise CoreMaintError(rc, "cm_server_run_trace")
+        return lat, rnd, wall.value
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().cm_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

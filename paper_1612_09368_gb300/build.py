@@ -13,7 +13,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcoremaint.so")
-SOURCES = ["cm_capi.cu", "cm_maintain.cu", "cm_iterate.cu", "cm_store.cu", "cm_noalloc.cu"]
+SOURCES = ["cm_capi.cu", "cm_maintain.cu", "cm_iterate.cu", "cm_store.cu", "cm_noalloc.cu", "cm_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 

@@ -1136,6 +1136,7 @@ struct cm_step {
     StepSig sig{};
     bool captured = false;
     long long captures = 0, replays = 0, fallbacks = 0;
+    long long fixed_kernels = 0;                // kernel nodes outside the loop bodies
 };
 
 static void step_default_config(const cm_graph* h, cm_step_config* c) {
@@ -1257,6 +1258,7 @@ static cudaError_t capture_phase(cm_step* s, int phase) {
     cudaError_t e;
     unsigned long long* kp = s->dK + phase;
     unsigned long long* np = &h->ctl->nrem;
+    s->fixed_kernels += (op == CM_OP_INSERT ? 10 : 5) + (h->dbases ? 1 : 0);
     if ((e = phase_begin(h->ctl, s->dLog, phase, cs)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->bset, 0xFF, h->bset_size * sizeof(BSet), cs)) != cudaSuccess) return e;
     if ((e = ingest_a(s->dE[phase], kmax, kp, g, h->bset, h->bset_size - 1, h->ctl, cs)) != cudaSuccess) return e;
@@ -1286,6 +1288,9 @@ static int step_capture(cm_step* s) {
     step_release_graph(s);
     DevGraph g = h->g;
     g.n = h->n;
+    s->fixed_kernels = 1;
+    for (int p = 0; p < 2; p++)
+        if ((p == 0 ? s->max_ins : s->max_del) > 0) s->fixed_kernels += h->dbases ? 2 : 1;
     cudaError_t e = cudaStreamBeginCapture(s->cs, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) e = step_begin(h->ctl, s->dLog, s->cs);
     for (int p = 0; p < 2 && e == cudaSuccess; p++) {
@@ -1556,8 +1561,9 @@ static int step_run_staged(cm_step* s, const long long k[2], int64_t* applied[2]
     CK(h, cudaGraphLaunch(s->exec, h->stream));
     CK(h, cudaEventRecord(h->ev[3], h->stream));
     s->replays++;
-    h->launches += 1;
     rc = step_finish(s, k, applied);
+    // kernels the replay ran: the fixed nodes and two per loop pass
+    h->launches += s->fixed_kernels + 2 * (long long)(s->hLog->passes[0] + s->hLog->passes[1]);
     if (rc) return rc;
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);

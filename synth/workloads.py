@@ -13,8 +13,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (DELETE, GRAPH, INSERT, PREFERENTIAL, UNIFORM, VDELETE, VINSERT, DynGraph, ba, er, rmat, stream,
-               uniform)
+from . import (ARRIVAL, DELETE, GRAPH, INSERT, PREFERENTIAL, UNIFORM, VDELETE, VINSERT, DynGraph, ba, er, rmat,
+               static_sample_delete, static_sample_insert, stream, uniform)
+from . import grid as _grid
 from . import ba_many as _ba_many
 
 EDGE_UNIFORM = PREFERENTIAL   # "a uniform random existing edge" is the degree-proportional delete law
@@ -134,3 +135,65 @@ def ba_many(ngraphs: int = 512, rounds: int = 1, cfg: int = 4, nmin_exp: float =
             bseeds[r, gi] = stream(cfg, gi, r + 1, INSERT)
     edges, eoff, ins, dele = _ba_many(ns, ms, gseeds, kins, kdel, bseeds)
     return {"ns": ns, "ms": ms, "edges": edges, "eoff": eoff, "ins": ins, "dele": dele, "kins": kins, "kdel": kdel}
+
+
+def serving_graphs(cfg: int = 5, scale: int = 22, edge_factor: int = 16, side: int = 2048,
+                   shortcut_frac: float = 0.01):
+    """The resident graphs of the serving workload: an R-MAT graph and a
+    side x side 4-neighbour grid plus shortcut_frac x its edge count of
+    uniform random long-range pairs.  Returns [(n, edges), (n, edges)]."""
+    e0 = rmat(scale, edge_factor, stream(cfg, 0, 0, GRAPH))
+    nshort = int(round(shortcut_frac * 2 * side * (side - 1)))
+    e1 = _grid(side, nshort, stream(cfg, 1, 0, GRAPH))
+    return [(1 << scale, e0), (side * side, e1)]
+
+
+def serving_trace(graphs, rate: float, duration_s: float, cfg: int = 5, trace: int = 0, median: float = 200.0,
+                  sigma: float = 1.5, lo: int = 10, hi: int = 10 ** 5, frac_insert: float = 0.7):
+    """Open-loop request stream: Poisson arrivals at `rate` per second for
+    `duration_s`; each request targets a uniform graph, is an insert with
+    probability frac_insert, and carries a log-normal number of edges
+    (median `median`, log-space deviation `sigma`, clamped to [lo, hi]).
+    Inserts are distinct uniform pairs absent from the graph as given and
+    deletes distinct uniform edges of it, none shared between requests, so
+    the requests of a graph can be applied in any interleaving and each
+    applies exactly its edges.  Returns dict(arrival_ns, graph, op, counts,
+    edges, off) with `edges` concatenated in request order (local ids)."""
+    import math
+    s = stream(cfg, 0, trace, ARRIVAL)
+    arr, gr, op, cnt = [], [], [], []
+    t, i = 0.0, 0
+    ng = len(graphs)
+    while True:
+        t += -math.log(1.0 - uniform(s, 5 * i)) / rate
+        if t >= duration_s:
+            break
+        gr.append(min(ng - 1, int(ng * uniform(s, 5 * i + 1))))
+        op.append(0 if uniform(s, 5 * i + 2) < frac_insert else 1)
+        u1 = max(uniform(s, 5 * i + 3), 1e-300)
+        z = math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * uniform(s, 5 * i + 4))
+        cnt.append(int(min(hi, max(lo, round(median * math.exp(sigma * z))))))
+        arr.append(int(t * 1e9))
+        i += 1
+    gr = np.array(gr, dtype=np.int32)
+    op = np.array(op, dtype=np.int32)
+    cnt = np.array(cnt, dtype=np.int64)
+    pools = {}
+    for gi, (n, e) in enumerate(graphs):
+        need_i = int(cnt[(gr == gi) & (op == 0)].sum())
+        need_d = int(cnt[(gr == gi) & (op == 1)].sum())
+        pi = static_sample_insert(n, e, need_i, UNIFORM, stream(cfg, gi, trace, INSERT))
+        pd = static_sample_delete(n, e, need_d, PREFERENTIAL, stream(cfg, gi, trace, DELETE))
+        if len(pi) < need_i or len(pd) < need_d:
+            raise ValueError("graph too small for the trace's batches")
+        pools[(gi, 0)] = [pi, 0]
+        pools[(gi, 1)] = [pd, 0]
+    off = np.zeros(len(cnt) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(cnt)
+    edges = np.empty((int(off[-1]), 2), dtype=np.int32)
+    for j in range(len(cnt)):
+        p = pools[(int(gr[j]), int(op[j]))]
+        edges[off[j]:off[j + 1]] = p[0][p[1]:p[1] + cnt[j]]
+        p[1] += int(cnt[j])
+    return {"arrival_ns": np.array(arr, dtype=np.int64), "graph": gr, "op": op, "counts": cnt, "edges": edges,
+            "off": off}
