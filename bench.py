@@ -116,6 +116,21 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate(t_ms: float, units: float, ws: int, device):
+    """Whole-job numbers over the ranks of a multi-GPU run: the slowest
+    rank's timed region and the units every rank processed (each rank runs
+    its own replica, so per-rank work is fixed as ranks are added)."""
+    if ws <= 1:
+        return t_ms, units
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    uu = torch.tensor([units], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 def make_workload(args, rounds):
     from synth import workloads
     return workloads.rmat_rounds(rounds, scale=args.scale)
@@ -617,14 +632,7 @@ def main():
     torch.cuda.synchronize()
     clocks = clk.stop()
     t_ms = sum(ev0[s].elapsed_time(ev1[s]) for s in range(K))
-    if ws > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        uu = torch.tensor([units], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
-        t_ms, units_all = float(tt.item()), float(uu.item())
-    else:
-        units_all = units
+    t_ms, units_all = aggregate(t_ms, units, ws, dev)
     value = units_all / (t_ms / 1000.0)
 
     # e2e: host pinned inputs, copies and the core read-back inside the timed region
