@@ -116,6 +116,15 @@ def dist_env():
     return ws, rank, local
 
 
+def handle_options(args) -> dict:
+    """cm_options fields given as --options name=value,... (defaults otherwise)."""
+    out = {}
+    for kv in filter(None, (args.options or "").split(",")):
+        k, v = kv.split("=")
+        out[k.strip()] = int(v)
+    return out
+
+
 def aggregate(t_ms: float, units: float, ws: int, device):
     """Whole-job numbers over the ranks of a multi-GPU run: the slowest
     rank's timed region and the units every rank processed (each rank runs
@@ -139,6 +148,8 @@ def make_workload(args, rounds):
 def config_of(w, args):
     c = {"workload": w.name, **w.params, "vertices": w.n, "initial_edges": int(len(w.edges)),
          "l2": "flushed before every step (256 MiB write)", "parallelism": "replicas"}
+    if handle_options(args):
+        c["options"] = handle_options(args)
     return c
 
 
@@ -225,7 +236,7 @@ def run_sweep(args):
     gen_s = time.time() - t0
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    g = cm.CoreGraph(n, torch.from_numpy(e).to(dev), stream=stream)
+    g = cm.CoreGraph(n, torch.from_numpy(e).to(dev), stream=stream, **handle_options(args))
     create = g.stats()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     peak, peak_kind = load_peaks()
@@ -275,6 +286,7 @@ def run_sweep(args):
     line = {"metric": METRIC, "workload": f"rmat{args.scale}-sweep", "unit": UNIT, "n_gpus": 1,
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"rmat{args.scale}-sweep", "scale": args.scale, "edge_factor": 16,
+                       "options": handle_options(args),
                        "vertices": n, "edges": int(len(e)), "batch_sizes": list(sizes),
                        "laws": ["uniform", "degree-proportional"], "reps": args.reps,
                        "l2": "flushed before every timed call (256 MiB write)"},
@@ -312,7 +324,8 @@ def run_batched(args):
     stream = torch.cuda.Stream(dev)
     peak, peak_kind = load_peaks()
     with torch.cuda.stream(stream):
-        g = cm.CoreGraph(None, torch.from_numpy(w["edges"]).to(dev), multi=(ns, np.diff(eoff)), stream=stream)
+        g = cm.CoreGraph(None, torch.from_numpy(w["edges"]).to(dev), multi=(ns, np.diff(eoff)), stream=stream,
+                         **handle_options(args))
         create = g.stats()
         bases = g.bases()
         kins, kdel = w["kins"], w["kdel"]
@@ -472,7 +485,8 @@ def run_serving(args):
         keep = keep_u < lam / max(rates)
         idx = np.nonzero(keep)[0]
         edges = np.concatenate([full["edges"][full["off"][j]:full["off"][j + 1]] for j in idx])
-        hs = [cm.CoreGraph(n, torch.from_numpy(e).cuda(), stream=torch.cuda.Stream(), max_sms=sms // 2)
+        hs = [cm.CoreGraph(n, torch.from_numpy(e).cuda(), stream=torch.cuda.Stream(),
+                           **{"max_sms": sms // 2, **handle_options(args)})
               for n, e in graphs]
         torch.cuda.synchronize()
         with cm.Server(hs, args.budget, max_round_edges=args.max_round) as srv:
@@ -540,6 +554,7 @@ def main():
     ap.add_argument("--budget", type=int, default=1 << 30)
     ap.add_argument("--max-round", dest="max_round", type=int, default=1 << 20)
     ap.add_argument("--graphs", type=int, default=512)
+    ap.add_argument("--options", default="", help="cm_options fields, e.g. block_slots=256,hub_slots=4096")
     ap.add_argument("--scale", type=int, default=None)
     ap.add_argument("--sizes", default="1000,10000,100000,1000000")
     ap.add_argument("--reps", type=int, default=3)
@@ -574,7 +589,7 @@ def main():
     w = make_workload(args, W + K + e2e_rounds)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    g = cm.CoreGraph(w.n, torch.from_numpy(w.edges).to(dev), stream=stream)
+    g = cm.CoreGraph(w.n, torch.from_numpy(w.edges).to(dev), stream=stream, **handle_options(args))
 
     def to_dev(r):
         off = np.zeros(len(r.vnbrs) + 1, np.int64)

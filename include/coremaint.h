@@ -81,6 +81,9 @@ typedef struct cm_options {
     int32_t block_mode_leave; /* single block -> grid after an iteration touching more (8192) */
     int32_t hub_slots;      /* grid mode: a vertex with at least this many adjacency slots is scanned by
                                every block in chunks of 2048 (16384; negative = never) */
+    int32_t block_slots;    /* a vertex with at least this many slots (below hub_slots) is scanned by a
+                               whole block instead of one warp (default 4096) */
+    int32_t reserved;
 } cm_options;
 
 /* Test hook: every grid barrier of the next maintenance launch waits for
@@ -257,7 +260,7 @@ typedef struct cm_step_config {
     int32_t block_mode_leave;
     int32_t hub_slots;         /* frontier granularity: grid-wide chunked scans from this many slots (-1 never) */
     int32_t blocks_per_sm;     /* block shape of the grid-mode launch: resident 512-thread blocks per SM (0 = max) */
-    int32_t reserved;
+    int32_t block_slots;       /* frontier granularity: block-wide scans from this many slots (0 = 4096) */
 } cm_step_config;
 
 /* max_insert / max_delete: capacity (edges) of the step's two batches.
@@ -289,11 +292,14 @@ typedef struct cm_tune_report {
     int32_t reps;     /* replays per configuration */
 } cm_tune_report;
 
-/* Autotuner: times the step's current configuration and a fixed grid of
- * candidates (hub_slots in {4096, 16384, 65536, never} x blocks_per_sm in
- * {1, 2} x three execution-mode threshold sets) on the given batches,
- * `reps` replays each (median), restoring the graph's device state and the
- * batch before every replay, and keeps the fastest on the step.  The graph
+/* Autotuner: times the step's current configuration, then tunes one knob
+ * at a time (coordinate descent, 12 candidates): hub_slots in {4096, 16384,
+ * 65536, never}, block_slots in {256, 1024, 4096}, blocks_per_sm in {1, 2},
+ * and three execution-mode threshold sets, each knob keeping the fastest
+ * value with the others at the best found so far.  Each candidate is timed
+ * on the given batches, `reps` replays (median), restoring the graph's
+ * device state and the batch before every replay; the fastest is kept on
+ * the step.  The graph
  * is left exactly as before the call.  Needs device memory for one copy of
  * the graph's state.  Same batch arguments and errors as cm_step_run. */
 int cm_step_autotune(cm_step* s, const int64_t* ins_counts, const int32_t* ins_edges, const int64_t* del_counts,

@@ -69,6 +69,7 @@ struct cm_graph {
     HubItem* HQ = nullptr;
     HubItem* PQ = nullptr;
     int32_t hub_len = 16384;
+    int32_t block_len = 4096;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -328,6 +329,7 @@ extern "C" void cm_default_options(cm_options* o) {
     o->block_mode_enter = 1024;
     o->block_mode_leave = 8192;
     o->hub_slots = 16384;
+    o->block_slots = 4096;
 }
 
 static void free_all(cm_graph* h) {
@@ -444,6 +446,7 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     h->small_work = h->opt.block_mode_enter > 0 ? h->opt.block_mode_enter : 1024;
     h->big_work = h->opt.block_mode_leave > 0 ? h->opt.block_mode_leave : 8192;
     h->hub_len = h->opt.hub_slots > 0 ? h->opt.hub_slots : h->opt.hub_slots < 0 ? 0 : 16384;
+    h->block_len = h->opt.block_slots >= 32 ? h->opt.block_slots : 4096;
     CK(h, cudaGetDevice(&h->device));
     CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     int coop = 0;
@@ -660,6 +663,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         p.HQ = h->HQ;
         p.PQ = h->PQ;
         p.hub_len = h->hub_len;
+        p.block_len = h->block_len;
         int blocks, threads;
         persistent_geometry(h, 0, nrem0, &blocks, &threads);
         p.expect = (uint32_t)blocks;
@@ -1146,6 +1150,7 @@ static void step_default_config(const cm_graph* h, cm_step_config* c) {
     c->block_mode_leave = (int32_t)h->big_work;
     c->hub_slots = h->hub_len > 0 ? h->hub_len : -1;
     c->blocks_per_sm = 0;
+    c->block_slots = h->block_len;
 }
 
 static StepSig step_signature(const cm_step* s) {
@@ -1199,6 +1204,7 @@ static MaintainParams step_params(const cm_step* s, int op, int* blocks, int* th
     p.HQ = h->HQ;
     p.PQ = h->PQ;
     p.hub_len = c.hub_slots > 0 ? c.hub_slots : c.hub_slots < 0 ? 0 : 16384;
+    p.block_len = c.block_slots >= 32 ? c.block_slots : 4096;
     int occ = maintain_blocks_per_sm(kGridThreadsHost);
     if (occ < 1) occ = 1;
     int bps = c.blocks_per_sm > 0 && c.blocks_per_sm < occ ? c.blocks_per_sm : occ;
@@ -1704,51 +1710,60 @@ extern "C" int cm_step_autotune(cm_step* s, const int64_t* ins_counts, const int
         for (int p = 0; p < 2; p++) dfree(h, raw[p], (size_t)k[p] * 8);
         return end_call(h, rc);
     }
-    // candidates: frontier granularity (hub threshold) x block shape
-    // (resident blocks per SM) x execution-mode thresholds
-    const int32_t hubs[] = {4096, 16384, 65536, -1};
-    const int32_t bps[] = {1, 2};
-    const int32_t modes[][3] = {{16384, 1024, 8192}, {65536, 4096, 32768}, {-1, 1024, 8192}};
-    std::vector<cm_step_config> cand;
+    // coordinate descent over the knobs, in this order: frontier
+    // granularity (hub threshold, then block-scan threshold), block shape
+    // (resident blocks per SM), execution-mode thresholds; each knob takes
+    // the best of its values with the others at the best found so far
     const cm_step_config first = s->cfg;
-    cand.push_back(first);
-    for (int32_t hb : hubs)
-        for (int32_t b : bps)
-            for (const auto& md : modes) {
-                cm_step_config c{};
-                c.hub_slots = hb;
-                c.blocks_per_sm = b;
-                c.block_mode_edges = md[0];
-                c.block_mode_enter = md[1];
-                c.block_mode_leave = md[2];
-                cand.push_back(c);
-            }
     double best_ms = 1e30, first_ms = 0;
     cm_step_config best = first;
     int tried = 0;
     int64_t* none[2] = {nullptr, nullptr};
     std::vector<float> t;
-    for (size_t ci = 0; ci < cand.size() && rc == CM_OK; ci++) {
-        s->cfg = cand[ci];
+    auto time_config = [&](const cm_step_config& c, double* med) -> int {
+        s->cfg = c;
         t.clear();
-        for (int r = 0; r < reps && rc == CM_OK; r++) {
-            if ((rc = snap_copy(h, z, false))) break;
+        for (int r = 0; r < reps; r++) {
+            int e = snap_copy(h, z, false);
+            if (e) return e;
             for (int p = 0; p < 2; p++)
                 if (k[p]) CK(h, cudaMemcpyAsync(s->dE[p], raw[p], (size_t)k[p] * 8, cudaMemcpyDeviceToDevice, h->stream));
             CK(h, cudaMemcpyAsync(s->dPre, s->hPre, (size_t)2 * (s->ng + 1) * 8, cudaMemcpyHostToDevice, h->stream));
             CK(h, cudaMemcpyAsync(s->dK, s->hK, 16, cudaMemcpyHostToDevice, h->stream));
             memset(&h->last, 0, sizeof(h->last));
-            if ((rc = step_run_staged(s, k, none))) break;
+            if ((e = step_run_staged(s, k, none))) return e;
             t.push_back((float)h->last.maintain_ms);
         }
-        if (rc) break;
         std::sort(t.begin(), t.end());
-        const double med = t[t.size() / 2];
+        *med = t[t.size() / 2];
         tried++;
-        if (ci == 0) first_ms = med;
-        if (med < best_ms) {
-            best_ms = med;
-            best = cand[ci];
+        return CM_OK;
+    };
+    rc = time_config(first, &first_ms);
+    best_ms = first_ms;
+    const int32_t hubs[] = {4096, 16384, 65536, -1};
+    const int32_t blocks[] = {256, 1024, 4096};
+    const int32_t bps[] = {1, 2};
+    const int32_t modes[][3] = {{16384, 1024, 8192}, {65536, 4096, 32768}, {-1, 1024, 8192}};
+    for (int knob = 0; knob < 4 && rc == CM_OK; knob++) {
+        const int nv = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 2 : 3;
+        cm_step_config base = best;
+        for (int v = 0; v < nv && rc == CM_OK; v++) {
+            cm_step_config c = base;
+            if (knob == 0) c.hub_slots = hubs[v];
+            else if (knob == 1) c.block_slots = blocks[v];
+            else if (knob == 2) c.blocks_per_sm = bps[v];
+            else {
+                c.block_mode_edges = modes[v][0];
+                c.block_mode_enter = modes[v][1];
+                c.block_mode_leave = modes[v][2];
+            }
+            double med = 0;
+            if ((rc = time_config(c, &med))) break;
+            if (med < best_ms) {
+                best_ms = med;
+                best = c;
+            }
         }
     }
     // leave the graph as it was before tuning and the step on the winner

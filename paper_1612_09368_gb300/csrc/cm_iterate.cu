@@ -52,7 +52,7 @@
 // The per-vertex bodies and the per-iteration vertex word are in cm_vertex.cuh.
 //
 // Per-vertex work of a wave is done by one warp per vertex (vertices fetched
-// dynamically); a vertex with at least kBigLen adjacency slots is deferred
+// dynamically); a vertex with at least P.block_len adjacency slots is deferred
 // and then processed by the whole block of the warp that fetched it.
 #include "cm_common.cuh"
 #include "cm_launch.h"
@@ -62,7 +62,6 @@ namespace cm {
 
 constexpr int kBlockThreads = 512;    // single-block mode
 constexpr int kGridThreads = 512;     // grid mode, per block
-constexpr int kBigLen = 256;
 constexpr int kMaxBig = 64;
 
 template <int MODE>
@@ -110,7 +109,7 @@ __device__ __forceinline__ bool push_hub(Ctl* C, HubItem* ring, int slot, unsign
 
 // Runs body(v, Group) for every vertex of ring[lo, hi): one warp per vertex
 // with dynamic fetching (counter *ctr, zeroed at every barrier).  A vertex
-// with at least kBigLen slots is deferred by the warp that fetched it and
+// with at least P.block_len slots is deferred by the warp that fetched it and
 // then processed by that warp's whole block (512 threads in either mode),
 // so a hub does not hold a wave on one warp.  In grid mode a vertex with at
 // least P.hub_len slots becomes a hub item of kind HUB instead (HUB >= 0),
@@ -139,7 +138,7 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
             if (MODE == 0 && HUB >= 0 && P.hub_len > 0 && len >= P.hub_len &&
                 push_hub(C, P.HQ, 4, vload64(&C->sprev[0]) >> 40, v, HUB, g.hs[v].x, g.off[v], len)) {
                 defer = 1;
-            } else if (len >= kBigLen) {
+            } else if (len >= P.block_len) {
                 int s = atomicAdd(&s_nbig, 1);
                 if (s < kMaxBig) {
                     s_big[s] = v;
