@@ -51,7 +51,7 @@ class cm_options(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int32), ("max_sms", ctypes.c_int32), ("block_mode_edges", ctypes.c_int32),
         ("spin_limit_ns", ctypes.c_int64), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("debug_flags", ctypes.c_int32), ("block_mode_enter", ctypes.c_int32), ("block_mode_leave", ctypes.c_int32),
-        ("hub_slots", ctypes.c_int32), ("block_slots", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("hub_slots", ctypes.c_int32), ("block_slots", ctypes.c_int32), ("block_slots_delete", ctypes.c_int32),
     ]
 
 

@@ -52,7 +52,8 @@
 // The per-vertex bodies and the per-iteration vertex word are in cm_vertex.cuh.
 //
 // Per-vertex work of a wave is done by one warp per vertex (vertices fetched
-// dynamically); a vertex with at least P.block_len adjacency slots is deferred
+// dynamically); a vertex with at least P.block_len adjacency slots (256 in
+// single-block mode) is deferred
 // and then processed by the whole block of the warp that fetched it.
 #include "cm_common.cuh"
 #include "cm_launch.h"
@@ -63,6 +64,7 @@ namespace cm {
 constexpr int kBlockThreads = 512;    // single-block mode
 constexpr int kGridThreads = 512;     // grid mode, per block
 constexpr int kMaxBig = 64;
+constexpr int kBlockLenSingle = 256;   // single-block mode: the block scans lists from this size
 
 template <int MODE>
 struct Barrier {
@@ -138,7 +140,7 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
             if (MODE == 0 && HUB >= 0 && P.hub_len > 0 && len >= P.hub_len &&
                 push_hub(C, P.HQ, 4, vload64(&C->sprev[0]) >> 40, v, HUB, g.hs[v].x, g.off[v], len)) {
                 defer = 1;
-            } else if (len >= P.block_len) {
+            } else if (len >= (MODE == 0 ? P.block_len : kBlockLenSingle)) {
                 int s = atomicAdd(&s_nbig, 1);
                 if (s < kMaxBig) {
                     s_big[s] = v;
