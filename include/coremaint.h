@@ -80,7 +80,7 @@ typedef struct cm_options {
     int32_t block_mode_enter; /* grid -> single block after an iteration touching <= this many items (1024) */
     int32_t block_mode_leave; /* single block -> grid after an iteration touching more (8192) */
     int32_t hub_slots;      /* grid mode: a vertex with at least this many adjacency slots is scanned by
-                               every block in chunks of 2048 (4096; negative = never) */
+                               all warps in chunks of 512 (1024; negative = never) */
     int32_t block_slots;    /* grid mode, insert: a vertex with at least this many slots (below hub_slots)
                                is scanned by a whole block instead of one warp (4096) */
     int32_t block_slots_delete; /* the same for delete calls (1024) */
@@ -258,7 +258,7 @@ typedef struct cm_step_config {
     int32_t block_mode_edges;  /* as in cm_options; negative = grid mode only */
     int32_t block_mode_enter;
     int32_t block_mode_leave;
-    int32_t hub_slots;         /* frontier granularity: grid-wide chunked scans from this many slots (0 = 4096, -1 never) */
+    int32_t hub_slots;         /* frontier granularity: grid-wide chunked scans from this many slots (0 = 1024, -1 never) */
     int32_t blocks_per_sm;     /* block shape of the grid-mode launch: resident 512-thread blocks per SM (0 = max) */
     int32_t block_slots;       /* frontier granularity: block-wide scans from this many slots, insert phase (0 = 4096) */
 } cm_step_config;
@@ -293,7 +293,7 @@ typedef struct cm_tune_report {
 } cm_tune_report;
 
 /* Autotuner: times the step's current configuration, then tunes one knob
- * at a time (coordinate descent, 12 candidates): hub_slots in {2048, 4096, 16384,
+ * at a time (coordinate descent, 12 candidates): hub_slots in {512, 1024, 4096,
  * never}, block_slots in {256, 1024, 4096}, blocks_per_sm in {1, 2},
  * and three execution-mode threshold sets, each knob keeping the fastest
  * value with the others at the best found so far.  Each candidate is timed

@@ -68,7 +68,7 @@ struct cm_graph {
     // grid-wide chunked scans of high-degree vertices (cm_iterate.cu)
     HubItem* HQ = nullptr;
     HubItem* PQ = nullptr;
-    int32_t hub_len = 4096;
+    int32_t hub_len = 1024;
     int32_t block_len = 4096, block_len_del = 1024;
 };
 
@@ -328,7 +328,7 @@ extern "C" void cm_default_options(cm_options* o) {
     o->block_mode_edges = 16384;
     o->block_mode_enter = 1024;
     o->block_mode_leave = 8192;
-    o->hub_slots = 4096;
+    o->hub_slots = 1024;
     o->block_slots = 4096;
     o->block_slots_delete = 1024;
 }
@@ -446,7 +446,7 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     h->small_edges = h->opt.block_mode_edges > 0 ? h->opt.block_mode_edges : h->opt.block_mode_edges < 0 ? 0 : 16384;
     h->small_work = h->opt.block_mode_enter > 0 ? h->opt.block_mode_enter : 1024;
     h->big_work = h->opt.block_mode_leave > 0 ? h->opt.block_mode_leave : 8192;
-    h->hub_len = h->opt.hub_slots > 0 ? h->opt.hub_slots : h->opt.hub_slots < 0 ? 0 : 4096;
+    h->hub_len = h->opt.hub_slots > 0 ? h->opt.hub_slots : h->opt.hub_slots < 0 ? 0 : 1024;
     h->block_len = h->opt.block_slots >= 32 ? h->opt.block_slots : 4096;
     h->block_len_del = h->opt.block_slots_delete >= 32 ? h->opt.block_slots_delete : 1024;
     CK(h, cudaGetDevice(&h->device));
@@ -1205,7 +1205,7 @@ static MaintainParams step_params(const cm_step* s, int op, int* blocks, int* th
     p.big_wave = p.big_work / 8 > 64 ? p.big_work / 8 : 64;
     p.HQ = h->HQ;
     p.PQ = h->PQ;
-    p.hub_len = c.hub_slots > 0 ? c.hub_slots : c.hub_slots < 0 ? 0 : 4096;
+    p.hub_len = c.hub_slots > 0 ? c.hub_slots : c.hub_slots < 0 ? 0 : 1024;
     p.block_len = op == CM_OP_INSERT ? (c.block_slots >= 32 ? c.block_slots : 4096) : h->block_len_del;
     int occ = maintain_blocks_per_sm(kGridThreadsHost);
     if (occ < 1) occ = 1;
@@ -1743,7 +1743,7 @@ extern "C" int cm_step_autotune(cm_step* s, const int64_t* ins_counts, const int
     };
     rc = time_config(first, &first_ms);
     best_ms = first_ms;
-    const int32_t hubs[] = {2048, 4096, 16384, -1};
+    const int32_t hubs[] = {512, 1024, 4096, -1};
     const int32_t blocks[] = {256, 1024, 4096};
     const int32_t bps[] = {1, 2};
     const int32_t modes[][3] = {{16384, 1024, 8192}, {65536, 4096, 32768}, {-1, 1024, 8192}};

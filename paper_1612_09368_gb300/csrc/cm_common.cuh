@@ -75,7 +75,7 @@ struct Resume {
 
 constexpr int kTails = 6;
 
-// A vertex whose adjacency is scanned by every block of a grid-mode launch,
+// A vertex whose adjacency is scanned by all warps of a grid-mode launch,
 // in chunks of kChunk slots (48 bytes; the lists are rings of kHubRing).
 // kind: HUB_FRONT (insert frontier: chunks sum CSD, the last one decides),
 // HUB_EVICT_INS / HUB_EVICT_DEL (eviction scans), HUB_EXPAND (visit the
@@ -90,7 +90,7 @@ struct __align__(16) HubItem {
     uint32_t done;                 // chunks finished
     int32_t pad;
 };
-constexpr int kChunk = 2048;                // slots per chunk: one 4-wide pass of 512 threads
+constexpr int kChunk = 512;                 // slots per chunk: four 4-wide passes of one warp
 constexpr unsigned long long kHubRing = 1ull << 16;
 constexpr unsigned long long kHubRingSafe = 1ull << 15;   // producers stop short of this backlog
 

@@ -124,10 +124,16 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
                                                 unsigned long long hi, Body body) {
     constexpr int NT = MODE == 0 ? kGridThreads : kBlockThreads;
     const int lane = lane_id();
+    // grid mode with hub lists taking every list a block would scan: no
+    // block-level deferral, hence no block barrier (warps go on to the next
+    // phase's work as soon as their own fetches run out)
+    const bool block_path = MODE == 1 || HUB < 0 || P.hub_len <= 0 || P.block_len < P.hub_len;
     __shared__ int s_big[kMaxBig];
     __shared__ int s_nbig;
-    if (threadIdx.x == 0) s_nbig = 0;
-    __syncthreads();
+    if (block_path) {
+        if (threadIdx.x == 0) s_nbig = 0;
+        __syncthreads();
+    }
     for (;;) {
         unsigned long long j = 0;
         if (lane == 0) j = atomicAdd(ctr, 1ull);
@@ -140,7 +146,7 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
             if (MODE == 0 && HUB >= 0 && P.hub_len > 0 && len >= P.hub_len &&
                 push_hub(C, P.HQ, 4, vload64(&C->sprev[0]) >> 40, v, HUB, g.hs[v].x, g.off[v], len)) {
                 defer = 1;
-            } else if (len >= (MODE == 0 ? P.block_len : kBlockLenSingle)) {
+            } else if (block_path && len >= (MODE == 0 ? P.block_len : kBlockLenSingle)) {
                 int s = atomicAdd(&s_nbig, 1);
                 if (s < kMaxBig) {
                     s_big[s] = v;
@@ -151,6 +157,7 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
         if (__shfl_sync(0xffffffffu, defer, 0)) continue;
         body(v, WarpGroup{});
     }
+    if (!block_path) return;
     __syncthreads();
     const int nb = min(s_nbig, kMaxBig);
     for (int b = 0; b < nb; b++) {
@@ -159,10 +166,13 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
     }
 }
 
-// Grid mode: every block takes chunks of the hub items queued in the
-// previous wave (HQ) and of the expansion items (PQ): the ranges between the
-// last two barrier snapshots, in the packed (items << 40 | chunks) form.
-//   HUB_FRONT: the chunk's share of CSD goes to the item; the block that
+// Grid mode: every warp takes chunks (kChunk slots) of the hub items queued
+// in the previous wave (HQ) and of the expansion items (PQ): the ranges
+// between the last two barrier snapshots, in the packed (items << 40 |
+// chunks) form.  Chunks are equal-sized units of work fetched one at a time,
+// so a wave's long lists spread over all warps and no block barrier is
+// involved.
+//   HUB_FRONT: the chunk's share of CSD goes to the item; the warp that
 //     finishes the last chunk adds the sum to the support word at once
 //     (flagging the vertex processed, as a whole-list scan would) and either
 //     queues an expansion item (support > k) or evicts the vertex.
@@ -173,50 +183,42 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
 // land before or after the CSD sum in any order, and a processed hub whose
 // count later falls to k is evicted by the decrement that does it.
 __device__ __noinline__ void hub_chunks(const DevGraph& g, Ctl* C, const MaintainParams& P, uint32_t e,
-                                           LocalStats& ls) {
-    using BG = BlockGroup<kGridThreads>;
+                                        LocalStats& ls) {
+    using WG = WarpGroup;
     const unsigned long long hq_lo = vload64(&C->sprev[0]), hq_hi = vload64(&C->stail[4]);
     const unsigned long long pq_lo = vload64(&C->sprev[1]), pq_hi = vload64(&C->stail[5]);
     const unsigned long long nh = (hq_hi & kChunkMask) - (hq_lo & kChunkMask);
     const unsigned long long np = (pq_hi & kChunkMask) - (pq_lo & kChunkMask);
     if (nh + np == 0) return;
-    __shared__ unsigned long long s_j;
-    __shared__ unsigned long long s_item;
-    __shared__ int s_expand_all;
     const int lane = lane_id();
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_j = atomicAdd(&C->pc[4], 1ull);
-        __syncthreads();
-        const unsigned long long j = s_j;
+        unsigned long long j = 0;
+        if (lane == 0) j = atomicAdd(&C->pc[4], 1ull);
+        j = __shfl_sync(0xffffffffu, j, 0);
         if (j >= nh + np) break;
         const bool from_h = j < nh;
         HubItem* ring = from_h ? P.HQ : P.PQ;
         const unsigned long long gc = from_h ? (hq_lo & kChunkMask) + j : (pq_lo & kChunkMask) + (j - nh);
-        if (threadIdx.x < 32) {
-            // 32-way search for the last item whose first chunk is <= gc
-            unsigned long long lo = (from_h ? hq_lo : pq_lo) >> 40, hi = (from_h ? hq_hi : pq_hi) >> 40;
-            for (int guard = 0; guard < 16 && hi - lo > 1; guard++) {
-                const unsigned long long step = (hi - lo + 31) / 32;
-                const unsigned long long idx = lo + (unsigned long long)lane * step;
-                const bool le = idx < hi && ring[idx & (kHubRing - 1)].c0 <= gc;
-                const unsigned int b = __ballot_sync(0xffffffffu, le);
-                const int last = 31 - __clz(b);   // lane 0 always qualifies
-                lo = lo + (unsigned long long)last * step;
-                hi = min(lo + step, hi);
-            }
-            if (lane == 0) s_item = lo;
+        // 32-way search for the last item whose first chunk is <= gc
+        unsigned long long lo = (from_h ? hq_lo : pq_lo) >> 40, hi = (from_h ? hq_hi : pq_hi) >> 40;
+        for (int guard = 0; guard < 16 && hi - lo > 1; guard++) {
+            const unsigned long long step = (hi - lo + 31) / 32;
+            const unsigned long long idx = lo + (unsigned long long)lane * step;
+            const bool le = idx < hi && ring[idx & (kHubRing - 1)].c0 <= gc;
+            const unsigned int bal = __ballot_sync(0xffffffffu, le);
+            const int last = 31 - __clz(bal);   // lane 0 always qualifies
+            lo = lo + (unsigned long long)last * step;
+            hi = min(lo + step, hi);
         }
-        __syncthreads();
-        HubItem* it = &ring[s_item & (kHubRing - 1)];
+        HubItem* it = &ring[lo & (kHubRing - 1)];
         const int v = it->v, kind = it->kind, k = it->k, len = it->len, nch = it->nch;
         const long long off = it->off;
         const int ci = (int)(gc - it->c0);
         const int s0 = ci * kChunk, s1 = min(s0 + kChunk, len);
         if (kind == HUB_FRONT) {
-            const int part = BG::sum(csd_part<BG>(g, k, off, s0, s1));
-            if (threadIdx.x == 0) {
-                s_expand_all = 0;
+            const int part = WG::sum(csd_part<WG>(g, k, off, s0, s1));
+            int expand_all = 0;
+            if (lane == 0) {
                 atomicAdd(&it->acc, part);
                 __threadfence();
                 if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
@@ -228,22 +230,21 @@ __device__ __noinline__ void hub_chunks(const DevGraph& g, Ctl* C, const Maintai
                     ls.vis++;
                     ls.visl += len;
                     if (oc + acc > k) {
-                        if (!push_hub(C, P.PQ, 5, pq_hi >> 40, v, HUB_EXPAND, k, off, len)) s_expand_all = 1;
+                        if (!push_hub(C, P.PQ, 5, pq_hi >> 40, v, HUB_EXPAND, k, off, len)) expand_all = 1;
                     } else {
                         const unsigned long long q = atomicAdd(&C->tail[1], 1ull);
                         P.EQ[q & P.qmask] = v;
                     }
                 }
             }
-            __syncthreads();
-            if (s_expand_all) expand_range<BG>(g, C, P, k, off, 0, len, e);   // expansion list full
+            if (__shfl_sync(0xffffffffu, expand_all, 0)) expand_range<WG>(g, C, P, k, off, 0, len, e);   // list full
         } else if (kind == HUB_EXPAND) {
-            expand_range<BG>(g, C, P, k, off, s0, s1, e);
+            expand_range<WG>(g, C, P, k, off, s0, s1, e);
         } else {
-            if (kind == HUB_EVICT_INS) evict_ins_range<BG>(g, C, P, k, off, s0, s1, e);
-            else evict_del_range<BG>(g, C, P, k, off, s0, s1, e);
-            __syncthreads();
-            if (threadIdx.x == 0) {
+            if (kind == HUB_EVICT_INS) evict_ins_range<WG>(g, C, P, k, off, s0, s1, e);
+            else evict_del_range<WG>(g, C, P, k, off, s0, s1, e);
+            __syncwarp();
+            if (lane == 0) {
                 __threadfence();
                 if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
                     if (kind == HUB_EVICT_DEL) g.hs[v].x = k - 1;

@@ -37,10 +37,14 @@ __device__ __forceinline__ uint32_t wz(unsigned long long x) { return (uint32_t)
 __device__ __forceinline__ int32_t ww(unsigned long long x) { return (int32_t)(uint32_t)(x >> 32); }
 
 // Stamps v's word with iteration e if it is older (count 0, no flags).
-// Retries are bounded; past the bound an error is recorded.
-__device__ __forceinline__ void make_current(const DevGraph& g, Ctl* C, int v, uint32_t e) {
+// `seen` is a value of the word the caller already read (from the 16-byte
+// vertex gather), which saves a load: a word stamped e stays stamped e for
+// the rest of the iteration.  Retries are bounded; past the bound an error
+// is recorded.
+__device__ __forceinline__ void make_current(const DevGraph& g, Ctl* C, int v, uint32_t e, unsigned long long seen) {
+    if (same_iter(wz(seen), e)) return;
     unsigned long long* p = iter_word(g, v);
-    unsigned long long old = vload64(p);
+    unsigned long long old = seen;
     const unsigned long long fresh = (unsigned long long)(e << 2);
     for (int tries = 0; tries < (1 << 20); tries++) {
         if (same_iter(wz(old), e)) return;
@@ -50,23 +54,37 @@ __device__ __forceinline__ void make_current(const DevGraph& g, Ctl* C, int v, u
     }
     atomicCAS(&C->error, 0, E_ITER_LIMIT);
 }
+__device__ __forceinline__ void make_current(const DevGraph& g, Ctl* C, int v, uint32_t e) {
+    make_current(g, C, v, e, vload64(iter_word(g, v)));
+}
+__device__ __forceinline__ unsigned long long word_of(const int4& h) {
+    return ((unsigned long long)(uint32_t)h.w << 32) | (uint32_t)h.z;
+}
 
 // Adds delta to v's count and low_add to its flag bits (only bits that are
 // clear); returns the previous (flags, count) of iteration e.
 __device__ __forceinline__ void add_word(const DevGraph& g, Ctl* C, int v, uint32_t e, int32_t delta,
-                                         uint32_t low_add, uint32_t& oflags, int32_t& ocount) {
-    make_current(g, C, v, e);
+                                         uint32_t low_add, uint32_t& oflags, int32_t& ocount,
+                                         unsigned long long seen) {
+    make_current(g, C, v, e, seen);
     unsigned long long old =
         atomicAdd(iter_word(g, v), ((unsigned long long)(uint32_t)delta << 32) + (unsigned long long)low_add);
     oflags = wz(old) & 3u;
     ocount = ww(old);
 }
+__device__ __forceinline__ void add_word(const DevGraph& g, Ctl* C, int v, uint32_t e, int32_t delta,
+                                         uint32_t low_add, uint32_t& oflags, int32_t& ocount) {
+    add_word(g, C, v, e, delta, low_add, oflags, ocount, vload64(iter_word(g, v)));
+}
 
 // Marks v visited in iteration e; true if this call did it.
-__device__ __forceinline__ bool visit(const DevGraph& g, Ctl* C, int v, uint32_t e) {
-    make_current(g, C, v, e);
+__device__ __forceinline__ bool visit(const DevGraph& g, Ctl* C, int v, uint32_t e, unsigned long long seen) {
+    make_current(g, C, v, e, seen);
     unsigned long long old = atomicOr(iter_word(g, v), (unsigned long long)kVisited);
     return (wz(old) & kVisited) == 0;
+}
+__device__ __forceinline__ bool visit(const DevGraph& g, Ctl* C, int v, uint32_t e) {
+    return visit(g, C, v, e, vload64(iter_word(g, v)));
 }
 
 // ---------------------------------------------------------------- thread groups
@@ -150,7 +168,7 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
-            bool p = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e);
+            bool p = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
             warp_push(&C->tail[0], P.VQ, P.qmask, p, w[q]);
         }
     SCAN4_END
@@ -175,7 +193,7 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
             if (h[q].x == k && h[q].y > k && !gone) {
                 uint32_t of;
                 int32_t oc;
-                add_word(g, C, w[q], e, -1, 0u, of, oc);
+                add_word(g, C, w[q], e, -1, 0u, of, oc, word_of(h[q]));
                 p = (of & kProcessed) && oc == k + 1;
             }
             warp_push(&C->tail[1], P.EQ, P.qmask, p, w[q]);
@@ -209,7 +227,7 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
             if (h[q].x == k && !gone && c[q] != e) {
                 uint32_t of;
                 int32_t oc;
-                add_word(g, C, w[q], e, 1, 0u, of, oc);
+                add_word(g, C, w[q], e, 1, 0u, of, oc, word_of(h[q]));
                 p = oc + 1 == thr;
                 if (p) g.chg[w[q]] = e;
             }

@@ -42,7 +42,7 @@ def test_default_options_without_gpu(so):
     o = cm.cm_default_options()
     assert (o.slack_pct, o.min_cap, o.block_threads, o.spin_limit_ns) == (25, 4, 512, 4_000_000_000)
     assert (o.block_mode_edges, o.block_mode_enter, o.block_mode_leave) == (16384, 1024, 8192)
-    assert (o.hub_slots, o.block_slots, o.block_slots_delete) == (4096, 4096, 1024)
+    assert (o.hub_slots, o.block_slots, o.block_slots_delete) == (1024, 4096, 1024)
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
