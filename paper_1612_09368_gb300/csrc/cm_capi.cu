@@ -67,7 +67,8 @@ struct cm_graph {
     long long small_edges = 16384, small_work = 1024, big_work = 8192;
     // grid-wide chunked scans of high-degree vertices (cm_iterate.cu)
     HubItem* HQ = nullptr;
-    HubItem* PQ = nullptr;
+    unsigned long long* TQ = nullptr;   // grid-mode task queue (TASK_EMPTY = all ones when free)
+    unsigned long long tq_size = 0;
     int32_t hub_len = 1024;
     int32_t block_len = 4096, block_len_del = 1024;
 };
@@ -260,6 +261,26 @@ static int ensure_index(cm_graph* h, long long adding) {
     return CM_OK;
 }
 
+// Task queue of the grid-mode search: room for every vertex entering the
+// frontier and being evicted once per iteration, plus the chunk tasks of
+// high-degree lists (three passes per list, at least 128 slots per hub) and
+// the claims warps make past the tail.
+static int ensure_tasks(cm_graph* h) {
+    const unsigned long long need =
+        pow2_at_least(2ull * (unsigned long long)h->ncap + (unsigned long long)h->g.adj_cap / 32 + (1ull << 18));
+    if (need <= h->tq_size) return CM_OK;
+    unsigned long long* q = (unsigned long long*)dalloc(h, need * 8);
+    if (!q) return set_err(h, CM_ERR_OOM, "out of device memory for a task queue of %llu slots", need);
+    CK(h, cudaMemsetAsync(q, 0xFF, need * 8, h->stream));
+    if (h->TQ) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        dfree(h, h->TQ, h->tq_size * 8);
+    }
+    h->TQ = q;
+    h->tq_size = need;
+    return CM_OK;
+}
+
 // Batch buffers for k edges: staging copy, dedupe set, remaining lists.
 static int ensure_batch(cm_graph* h, long long k) {
     if (k > h->batch_cap) {
@@ -357,7 +378,7 @@ static void free_all(cm_graph* h) {
     dfree(h, h->CQ, qn * 4);
     dfree(h, h->OVL, qn * 4);
     dfree(h, h->HQ, kHubRing * sizeof(HubItem));
-    dfree(h, h->PQ, kHubRing * sizeof(HubItem));
+    dfree(h, h->TQ, h->tq_size * 8);
     dfree(h, h->dbatch, (size_t)h->batch_cap * 8);
     dfree(h, h->bset, h->bset_size * sizeof(BSet));
     dfree(h, h->R0, (size_t)h->rcap * sizeof(REdge));
@@ -446,7 +467,8 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     h->small_edges = h->opt.block_mode_edges > 0 ? h->opt.block_mode_edges : h->opt.block_mode_edges < 0 ? 0 : 16384;
     h->small_work = h->opt.block_mode_enter > 0 ? h->opt.block_mode_enter : 1024;
     h->big_work = h->opt.block_mode_leave > 0 ? h->opt.block_mode_leave : 8192;
-    h->hub_len = h->opt.hub_slots > 0 ? h->opt.hub_slots : h->opt.hub_slots < 0 ? 0 : 1024;
+    h->hub_len = h->opt.hub_slots > 0 ? (h->opt.hub_slots < 128 ? 128 : h->opt.hub_slots)
+                                      : h->opt.hub_slots < 0 ? 0 : 1024;
     h->block_len = h->opt.block_slots >= 32 ? h->opt.block_slots : 4096;
     h->block_len_del = h->opt.block_slots_delete >= 32 ? h->opt.block_slots_delete : 1024;
     CK(h, cudaGetDevice(&h->device));
@@ -458,8 +480,7 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     CK(h, cudaMalloc(&h->ctl, sizeof(Ctl)));
     CK(h, cudaMemset(h->ctl, 0, sizeof(Ctl)));
     h->HQ = (HubItem*)dalloc(h, kHubRing * sizeof(HubItem));
-    h->PQ = (HubItem*)dalloc(h, kHubRing * sizeof(HubItem));
-    if (!h->HQ || !h->PQ) return set_err(h, CM_ERR_OOM, "out of device memory for the hub lists");
+    if (!h->HQ) return set_err(h, CM_ERR_OOM, "out of device memory for the hub items");
     CK(h, cudaMallocHost(&h->hctl, sizeof(Ctl)));
     memset(h->hctl, 0, sizeof(Ctl));
     h->g.slack_pct = h->opt.slack_pct;
@@ -662,8 +683,10 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         p.small_work = h->small_work;
         p.big_work = h->big_work;
         p.big_wave = h->big_work / 8 > 64 ? h->big_work / 8 : 64;
+        if ((rc = ensure_tasks(h))) return rc;
         p.HQ = h->HQ;
-        p.PQ = h->PQ;
+        p.TQ = h->TQ;
+        p.tqmask = h->tq_size - 1;
         p.hub_len = h->hub_len;
         p.block_len = op == CM_OP_INSERT ? h->block_len : h->block_len_del;
         int blocks, threads;
@@ -1117,6 +1140,8 @@ struct StepSig {   // everything a captured step bakes in
     int32_t* CQ;
     int32_t* OVL;
     unsigned long long qmask;
+    unsigned long long* TQ;
+    unsigned long long tq_size;
     cudaStream_t stream;
     cm_step_config cfg;
 };
@@ -1170,6 +1195,8 @@ static StepSig step_signature(const cm_step* s) {
     z.CQ = h->CQ;
     z.OVL = h->OVL;
     z.qmask = h->qmask;
+    z.TQ = h->TQ;
+    z.tq_size = h->tq_size;
     z.stream = h->stream;
     z.cfg = s->cfg;
     return z;
@@ -1204,8 +1231,9 @@ static MaintainParams step_params(const cm_step* s, int op, int* blocks, int* th
     p.big_work = c.block_mode_leave > 0 ? c.block_mode_leave : 8192;
     p.big_wave = p.big_work / 8 > 64 ? p.big_work / 8 : 64;
     p.HQ = h->HQ;
-    p.PQ = h->PQ;
-    p.hub_len = c.hub_slots > 0 ? c.hub_slots : c.hub_slots < 0 ? 0 : 1024;
+    p.TQ = h->TQ;
+    p.tqmask = h->tq_size - 1;
+    p.hub_len = c.hub_slots > 0 ? (c.hub_slots < 128 ? 128 : c.hub_slots) : c.hub_slots < 0 ? 0 : 1024;
     p.block_len = op == CM_OP_INSERT ? (c.block_slots >= 32 ? c.block_slots : 4096) : h->block_len_del;
     int occ = maintain_blocks_per_sm(kGridThreadsHost);
     if (occ < 1) occ = 1;
@@ -1450,6 +1478,7 @@ static int step_prepare(cm_step* s, long long kins) {
     if ((rc = ensure_index(h, kins))) return rc;
     const long long kmax = s->max_ins > s->max_del ? s->max_ins : s->max_del;
     if ((rc = ensure_batch(h, kmax))) return rc;
+    if ((rc = ensure_tasks(h))) return rc;
     if (h->epoch > 0x3F000000u) {   // 30-bit stamps about to wrap: clear them
         DevGraph& g = h->g;
         CK(h, cudaMemsetAsync(g.chg, 0, (size_t)h->n * 4, h->stream));

@@ -91,8 +91,8 @@ struct __align__(16) HubItem {
     int32_t pad;
 };
 constexpr int kChunk = 512;                 // slots per chunk: four 4-wide passes of one warp
-constexpr unsigned long long kHubRing = 1ull << 16;
-constexpr unsigned long long kHubRingSafe = 1ull << 15;   // producers stop short of this backlog
+constexpr unsigned long long kHubRing = 1ull << 20;
+constexpr unsigned long long kHubRingSafe = kHubRing - 4096;   // items in flight stay below this
 
 // Device control block, one per handle.  The barrier words and counters are
 // 64-bit and monotone within a launch where noted.
@@ -120,6 +120,11 @@ struct __align__(128) Ctl {
     int min_deg;                   // peel: smallest remaining degree
     int defer;                     // captured step: skip its remaining kernels (1 pool short, 2 error)
     unsigned long long passes;     // captured step: launch pairs of the current phase
+    // grid-mode task queue of the current search (reset before each search)
+    unsigned long long task_head;  // next slot a warp claims
+    unsigned long long task_tail;  // slots reserved by producers
+    unsigned long long task_done;  // tasks finished
+    unsigned long long hub_created, hub_finished;   // hub items of the current search
     Resume rs;
 };
 
@@ -202,6 +207,10 @@ __device__ __forceinline__ long long idx_insert(Bucket* idx, unsigned long long 
 }
 
 // ---------------------------------------------------------------- timing / sync
+__device__ __forceinline__ void vstore64(unsigned long long* p, unsigned long long v) {
+    *(volatile unsigned long long*)p = v;
+}
+
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

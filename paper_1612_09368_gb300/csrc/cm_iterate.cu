@@ -85,55 +85,23 @@ struct Barrier {
     }
 };
 
-// ---------------------------------------------------------------- hub lists
-constexpr unsigned long long kChunkMask = (1ull << 40) - 1;
-
-// Appends a hub item to list `slot` (4: HQ, 5: PQ) unless the list's backlog
-// since item `lo_items` (the oldest item still being consumed) nears the
-// ring size.  One thread calls it.
-__device__ __forceinline__ bool push_hub(Ctl* C, HubItem* ring, int slot, unsigned long long lo_items, int v,
-                                         int kind, int k, long long off, int len) {
-    if ((vload64(&C->tail[slot]) >> 40) - lo_items >= kHubRingSafe) return false;
-    const int nch = (len + kChunk - 1) / kChunk;
-    const unsigned long long old = atomicAdd(&C->tail[slot], (1ull << 40) | (unsigned long long)nch);
-    HubItem& it = ring[(old >> 40) & (kHubRing - 1)];
-    it.off = off;
-    it.c0 = old & kChunkMask;
-    it.v = v;
-    it.kind = kind;
-    it.k = k;
-    it.len = len;
-    it.nch = nch;
-    it.acc = 0;
-    it.done = 0u;
-    return true;
-}
-
+// ---------------------------------------------------------------- vertex loop (waves)
 // Runs body(v, Group) for every vertex of ring[lo, hi): one warp per vertex
 // with dynamic fetching (counter *ctr, zeroed at every barrier).  A vertex
-// with at least P.block_len slots is deferred by the warp that fetched it and
-// then processed by that warp's whole block (512 threads in either mode),
-// so a hub does not hold a wave on one warp.  In grid mode a vertex with at
-// least P.hub_len slots becomes a hub item of kind HUB instead (HUB >= 0),
-// which every block scans in chunks in the next wave.  Every thread of the
-// launch must call it.
-template <int MODE, int HUB, class Body>
-__device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P,
-                                                unsigned long long* ctr,
+// with at least P.block_len slots (kBlockLenSingle in single-block mode) is
+// deferred by the warp that fetched it and then processed by that warp's
+// whole block, so a long list does not hold a wave on one warp.  Every
+// thread of the launch must call it.
+template <int MODE, class Body>
+__device__ __forceinline__ void for_each_vertex(const DevGraph& g, const MaintainParams& P, unsigned long long* ctr,
                                                 const int32_t* ring, unsigned long long qm, unsigned long long lo,
                                                 unsigned long long hi, Body body) {
     constexpr int NT = MODE == 0 ? kGridThreads : kBlockThreads;
     const int lane = lane_id();
-    // grid mode with hub lists taking every list a block would scan: no
-    // block-level deferral, hence no block barrier (warps go on to the next
-    // phase's work as soon as their own fetches run out)
-    const bool block_path = MODE == 1 || HUB < 0 || P.hub_len <= 0 || P.block_len < P.hub_len;
     __shared__ int s_big[kMaxBig];
     __shared__ int s_nbig;
-    if (block_path) {
-        if (threadIdx.x == 0) s_nbig = 0;
-        __syncthreads();
-    }
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
     for (;;) {
         unsigned long long j = 0;
         if (lane == 0) j = atomicAdd(ctr, 1ull);
@@ -141,23 +109,16 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
         if (j >= hi - lo) break;
         const int v = ring[(lo + j) & qm];
         int defer = 0;
-        if (lane == 0) {
-            const int len = g.end[v];
-            if (MODE == 0 && HUB >= 0 && P.hub_len > 0 && len >= P.hub_len &&
-                push_hub(C, P.HQ, 4, vload64(&C->sprev[0]) >> 40, v, HUB, g.hs[v].x, g.off[v], len)) {
+        if (lane == 0 && g.end[v] >= (MODE == 0 ? P.block_len : kBlockLenSingle)) {
+            int s = atomicAdd(&s_nbig, 1);
+            if (s < kMaxBig) {
+                s_big[s] = v;
                 defer = 1;
-            } else if (block_path && len >= (MODE == 0 ? P.block_len : kBlockLenSingle)) {
-                int s = atomicAdd(&s_nbig, 1);
-                if (s < kMaxBig) {
-                    s_big[s] = v;
-                    defer = 1;
-                }
             }
         }
         if (__shfl_sync(0xffffffffu, defer, 0)) continue;
         body(v, WarpGroup{});
     }
-    if (!block_path) return;
     __syncthreads();
     const int nb = min(s_nbig, kMaxBig);
     for (int b = 0; b < nb; b++) {
@@ -166,93 +127,226 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, Ctl* C, const
     }
 }
 
-// Grid mode: every warp takes chunks (kChunk slots) of the hub items queued
-// in the previous wave (HQ) and of the expansion items (PQ): the ranges
-// between the last two barrier snapshots, in the packed (items << 40 |
-// chunks) form.  Chunks are equal-sized units of work fetched one at a time,
-// so a wave's long lists spread over all warps and no block barrier is
-// involved.
-//   HUB_FRONT: the chunk's share of CSD goes to the item; the warp that
+// ---------------------------------------------------------------- grid-mode task queue
+// In grid mode the search of an iteration (insert: positive search and
+// evictions; delete: evictions) runs without level barriers.  Every vertex
+// that enters the frontier or is evicted also becomes a task in a queue
+// (push_vertex), and warps claim tasks one at a time until the queue is
+// quiescent: every task pushed has finished.  The proof of the interleaved
+// search does not depend on the order in which vertices are processed, so
+// the waves of the single-block mode and this order reach the same cores.
+//
+// A vertex with at least P.hub_len slots becomes a hub item instead, whose
+// list is split into kChunk-slot chunk tasks that any warp may take:
+//   HUB_FRONT: each chunk adds its share of CSD to the item; the warp that
 //     finishes the last chunk adds the sum to the support word at once
-//     (flagging the vertex processed, as a whole-list scan would) and either
-//     queues an expansion item (support > k) or evicts the vertex.
-//   HUB_EVICT_INS / HUB_EVICT_DEL: the chunk's share of the eviction; the
-//     last chunk lowers the core (delete) and counts the vertex.
-//   HUB_EXPAND: the chunk's share of the frontier expansion.
+//     (setting the processed flag, as a whole-list scan would) and either
+//     queues an expansion item (support > k) or evicts the vertex;
+//   HUB_EXPAND: each chunk visits its share of the core-k neighbours;
+//   HUB_EVICT_INS / HUB_EVICT_DEL: each chunk evicts its share; the last one
+//     lowers the core (delete) and counts the vertex.
 // The support word tolerates the delay: decrements from evicted neighbours
 // land before or after the CSD sum in any order, and a processed hub whose
 // count later falls to k is evicted by the decrement that does it.
-__device__ __noinline__ void hub_chunks(const DevGraph& g, Ctl* C, const MaintainParams& P, uint32_t e,
-                                        LocalStats& ls) {
-    using WG = WarpGroup;
-    const unsigned long long hq_lo = vload64(&C->sprev[0]), hq_hi = vload64(&C->stail[4]);
-    const unsigned long long pq_lo = vload64(&C->sprev[1]), pq_hi = vload64(&C->stail[5]);
-    const unsigned long long nh = (hq_hi & kChunkMask) - (hq_lo & kChunkMask);
-    const unsigned long long np = (pq_hi & kChunkMask) - (pq_lo & kChunkMask);
-    if (nh + np == 0) return;
+
+// Creates a hub item and its chunk tasks (warp-collective); false if the
+// item ring is full (the caller then scans the list itself).
+__device__ __forceinline__ bool make_hub(Ctl* C, const MaintainParams& P, int v, int kind, int k, long long off,
+                                         int len) {
     const int lane = lane_id();
-    for (;;) {
-        unsigned long long j = 0;
-        if (lane == 0) j = atomicAdd(&C->pc[4], 1ull);
-        j = __shfl_sync(0xffffffffu, j, 0);
-        if (j >= nh + np) break;
-        const bool from_h = j < nh;
-        HubItem* ring = from_h ? P.HQ : P.PQ;
-        const unsigned long long gc = from_h ? (hq_lo & kChunkMask) + j : (pq_lo & kChunkMask) + (j - nh);
-        // 32-way search for the last item whose first chunk is <= gc
-        unsigned long long lo = (from_h ? hq_lo : pq_lo) >> 40, hi = (from_h ? hq_hi : pq_hi) >> 40;
-        for (int guard = 0; guard < 16 && hi - lo > 1; guard++) {
-            const unsigned long long step = (hi - lo + 31) / 32;
-            const unsigned long long idx = lo + (unsigned long long)lane * step;
-            const bool le = idx < hi && ring[idx & (kHubRing - 1)].c0 <= gc;
-            const unsigned int bal = __ballot_sync(0xffffffffu, le);
-            const int last = 31 - __clz(bal);   // lane 0 always qualifies
-            lo = lo + (unsigned long long)last * step;
-            hi = min(lo + step, hi);
+    const int nch = (len + kChunk - 1) / kChunk;
+    unsigned long long idx = 0, tb = 0;
+    int ok = 0;
+    if (lane == 0) {
+        if (vload64(&C->hub_created) - vload64(&C->hub_finished) < kHubRingSafe) {
+            idx = atomicAdd(&C->hub_created, 1ull);
+            HubItem* it = &P.HQ[idx & (kHubRing - 1)];
+            it->off = off;
+            it->c0 = 0;
+            it->v = v;
+            it->kind = kind;
+            it->k = k;
+            it->len = len;
+            it->nch = nch;
+            it->acc = 0;
+            it->done = 0u;
+            __threadfence();   // the item before its tasks
+            tb = atomicAdd(&C->task_tail, (unsigned long long)nch);
+            ok = 1;
         }
-        HubItem* it = &ring[lo & (kHubRing - 1)];
-        const int v = it->v, kind = it->kind, k = it->k, len = it->len, nch = it->nch;
-        const long long off = it->off;
-        const int ci = (int)(gc - it->c0);
-        const int s0 = ci * kChunk, s1 = min(s0 + kChunk, len);
-        if (kind == HUB_FRONT) {
-            const int part = WG::sum(csd_part<WG>(g, k, off, s0, s1));
-            int expand_all = 0;
-            if (lane == 0) {
-                atomicAdd(&it->acc, part);
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    tb = __shfl_sync(0xffffffffu, tb, 0);
+    if (!task_room(C, P, tb, (unsigned long long)nch)) return true;   // error recorded; the search stops
+    const unsigned long long base = ((idx & (kHubRing - 1)) << kTaskChunkBits);
+    for (int j = lane; j < nch; j += 32)
+        vstore64(&P.TQ[(tb + j) & P.tqmask], mk_task(T_CHUNK, base | (unsigned long long)j));
+    return true;
+}
+
+__device__ __forceinline__ int vload32i(const int* p) { return *(const volatile int*)p; }
+
+// One chunk task (warp-collective).
+__device__ __forceinline__ void run_chunk(const DevGraph& g, Ctl* C, const MaintainParams& P, uint32_t e,
+                                          LocalStats& ls, unsigned long long payload) {
+    using WG = WarpGroup;
+    const int lane = lane_id();
+    HubItem* it = &P.HQ[payload >> kTaskChunkBits];
+    const int ci = (int)(payload & ((1ull << kTaskChunkBits) - 1));
+    // the item was written by another SM: read it from L2
+    const int v = vload32i(&it->v), kind = vload32i(&it->kind), k = vload32i(&it->k);
+    const int len = vload32i(&it->len), nch = vload32i(&it->nch);
+    const long long off = (long long)vload64((const unsigned long long*)&it->off);
+    const int s0 = ci * kChunk, s1 = min(s0 + kChunk, len);
+    if (kind == HUB_FRONT) {
+        const int part = WG::sum(csd_part<WG>(g, k, off, s0, s1));
+        int decide = 0;   // 1 expand, 2 evict
+        if (lane == 0) {
+            atomicAdd(&it->acc, part);
+            __threadfence();
+            if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
                 __threadfence();
-                if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
+                const int acc = atomicAdd(&it->acc, 0);
+                uint32_t of;
+                int32_t oc;
+                add_word(g, C, v, e, acc, kProcessed, of, oc);
+                ls.vis++;
+                ls.visl += len;
+                decide = oc + acc > k ? 1 : 2;
+                atomicAdd(&C->hub_finished, 1ull);
+            }
+        }
+        decide = __shfl_sync(0xffffffffu, decide, 0);
+        if (decide == 1 && !make_hub(C, P, v, HUB_EXPAND, k, off, len))
+            expand_range<WG, true>(g, C, P, k, off, 0, len, e);
+        if (decide == 2) push_vertex<true>(C, P, lane == 0, v, 1);
+        return;
+    }
+    if (kind == HUB_EXPAND) expand_range<WG, true>(g, C, P, k, off, s0, s1, e);
+    else if (kind == HUB_EVICT_INS) evict_ins_range<WG, true>(g, C, P, k, off, s0, s1, e);
+    else evict_del_range<WG, true>(g, C, P, k, off, s0, s1, e);
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
+            if (kind == HUB_EVICT_DEL) g.hs[v].x = k - 1;
+            if (kind != HUB_EXPAND) {
+                ls.ev++;
+                ls.evl += len;
+            }
+            atomicAdd(&C->hub_finished, 1ull);
+        }
+    }
+}
+
+// Drains the task queue (every warp of the grid).  Returns false on error.
+// A warp claims up to kClaim consecutive slots with one atomic -- it doubles
+// its claim while its slots are ready at once and drops back to one slot
+// after it had to wait, so small searches keep every warp busy and large
+// ones touch the shared head counter less -- and reports its finished tasks
+// in batches, always before it waits on an empty slot (so a waiting warp
+// never holds back the quiescence test).
+constexpr int kClaim = 8;
+__device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const MaintainParams& P, uint32_t e,
+                                          LocalStats& ls) {
+    using WG = WarpGroup;
+    const int lane = lane_id();
+    const unsigned long long t_start = gtimer();
+    unsigned long long idx = 0, ndone = 0;
+    int left = 0, claim = 1;
+    bool waited = false;
+    for (;;) {
+        unsigned long long t = TASK_EMPTY;
+        int quit = 0;
+        if (lane == 0) {
+            if (left == 0) {
+                claim = waited ? 1 : min(2 * claim, kClaim);
+                waited = false;
+                idx = atomicAdd(&C->task_head, (unsigned long long)claim);
+                left = claim;
+            }
+            unsigned long long* slot = &P.TQ[idx & P.tqmask];
+            unsigned int nap = 32;
+            for (unsigned int spins = 0;; spins++) {
+                t = vload64(slot);
+                if (t != TASK_EMPTY) {
+                    vstore64(slot, TASK_EMPTY);   // free for the next search
+                    break;
+                }
+                waited = true;
+                if (ndone) {   // report before waiting
                     __threadfence();
-                    const int acc = atomicAdd(&it->acc, 0);
-                    uint32_t of;
-                    int32_t oc;
-                    add_word(g, C, v, e, acc, kProcessed, of, oc);
-                    ls.vis++;
-                    ls.visl += len;
-                    if (oc + acc > k) {
-                        if (!push_hub(C, P.PQ, 5, pq_hi >> 40, v, HUB_EXPAND, k, off, len)) expand_all = 1;
-                    } else {
-                        const unsigned long long q = atomicAdd(&C->tail[1], 1ull);
-                        P.EQ[q & P.qmask] = v;
+                    atomicAdd(&C->task_done, ndone);
+                    ndone = 0;
+                }
+                if ((spins & 3u) == 0) {
+                    // quiescent: every task pushed has finished (done read first)
+                    const unsigned long long d = vload64(&C->task_done);
+                    if (d == vload64(&C->task_tail) || vload32(&C->error)) {
+                        quit = 1;
+                        break;
+                    }
+                    if (gtimer() - t_start > P.limit_ns) {
+                        atomicCAS(&C->error, 0, E_BARRIER_TIMEOUT);
+                        quit = 1;
+                        break;
                     }
                 }
+                __nanosleep(nap);
+                if (nap < 2048) nap <<= 1;
             }
-            if (__shfl_sync(0xffffffffu, expand_all, 0)) expand_range<WG>(g, C, P, k, off, 0, len, e);   // list full
-        } else if (kind == HUB_EXPAND) {
-            expand_range<WG>(g, C, P, k, off, s0, s1, e);
+            idx++;
+            left--;
+        }
+        if (__shfl_sync(0xffffffffu, quit, 0)) break;
+        t = __shfl_sync(0xffffffffu, t, 0);
+        // acquire: the task's vertex data as its producers left it (measured
+        // necessary: without it a warp running consecutive claimed tasks
+        // reached wrong cores on small delete batches)
+        __threadfence();
+        const int type = (int)(t >> 62);
+        const unsigned long long payload = t & ((1ull << 62) - 1);
+        if (type == T_CHUNK) {
+            run_chunk(g, C, P, e, ls, payload);
         } else {
-            if (kind == HUB_EVICT_INS) evict_ins_range<WG>(g, C, P, k, off, s0, s1, e);
-            else evict_del_range<WG>(g, C, P, k, off, s0, s1, e);
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence();
-                if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
-                    if (kind == HUB_EVICT_DEL) g.hs[v].x = k - 1;
-                    ls.ev++;
-                    ls.evl += len;
-                }
+            const int v = (int)payload;
+            const int len = g.end[v];
+            const bool hub = P.hub_len > 0 && len >= P.hub_len;
+            if (type == T_FRONT) {
+                if (!hub || !make_hub(C, P, v, HUB_FRONT, g.hs[v].x, g.off[v], len))
+                    process_frontier<WG, true>(g, C, P, v, e, ls);
+            } else if (P.op == 0) {
+                if (!hub || !make_hub(C, P, v, HUB_EVICT_INS, g.hs[v].x, g.off[v], len))
+                    evict_insert_vertex<WG, true>(g, C, P, v, e, ls);
+            } else {
+                if (!hub || !make_hub(C, P, v, HUB_EVICT_DEL, g.hs[v].x, g.off[v], len))
+                    evict_delete_vertex<WG, true>(g, C, P, v, e, ls);
             }
         }
+        __syncwarp();
+        if (lane == 0) ndone++;   // this task's pushes precede the fence of the next report
+    }
+    return vload32(&C->error) == 0;
+}
+
+// Queues tasks for log entries [lo, hi) that are already in the log (a
+// search resumed from the single-block mode).  Every warp calls it.
+__device__ __forceinline__ void seed_tasks(Ctl* C, const MaintainParams& P, const int32_t* log, unsigned long long lo,
+                                           unsigned long long hi, int type) {
+    const int lane = lane_id();
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long base = lo + (unsigned long long)gwarp * 32; base < hi;
+         base += (unsigned long long)nwarps * 32) {
+        const unsigned long long cnt = min(32ull, hi - base);
+        unsigned long long tb = 0;
+        if (lane == 0) tb = atomicAdd(&C->task_tail, cnt);
+        tb = __shfl_sync(0xffffffffu, tb, 0);
+        if (task_room(C, P, tb, cnt) && (unsigned long long)lane < cnt)
+            vstore64(&P.TQ[(tb + lane) & P.tqmask],
+                     mk_task(type, (unsigned long long)(uint32_t)log[(base + lane) & P.qmask]));
     }
 }
 
@@ -348,10 +442,15 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     uint32_t e = *(volatile uint32_t*)&C->rs.epoch;
     const long long iters0 = *(volatile long long*)&C->rs.iters;
     unsigned long long vq_t = vload64(&C->tail[0]), eq_t = vload64(&C->tail[1]), cq_t = vload64(&C->tail[2]);
-    // hub and expansion lists queued in the last wave: between the last two
-    // barrier snapshots (empty at iteration boundaries)
-    auto hubs_pending = [&]() {
-        return vload64(&C->stail[4]) != vload64(&C->sprev[0]) || vload64(&C->stail[5]) != vload64(&C->sprev[1]);
+    // grid mode: the task queue starts empty for every search
+    auto reset_tasks = [&]() {
+        if (leader) {
+            C->task_head = 0;
+            C->task_tail = 0;
+            C->task_done = 0;
+            C->hub_created = 0;
+            C->hub_finished = 0;
+        }
     };
     LocalStats ls;
     long long iters = 0, rounds = 0, waves = 0, remsum = 0;
@@ -393,9 +492,10 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         int r = 0;
         for (;;) {
             if (r == 0 && fx) {
-                for_each_vertex<MODE, -1>(g, C, P, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
+                for_each_vertex<MODE>(g, P, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
                 fx = false;
             }
+            if (MODE == 0 && r == 0) reset_tasks();   // nobody pushes tasks before APPLY
             for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
                 long long i = base + lane;
                 if (i < (long long)nrem) claim_edge(g, Rc, i, r, e);
@@ -473,10 +573,9 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                 E.flags = 0;
             }
             warp_push_edge(&C->pc[1], Rn, valid && !sel, E);
-            unsigned long long* qt = P.op == 0 ? &C->tail[0] : &C->tail[1];
-            int32_t* q = P.op == 0 ? P.VQ : P.EQ;
-            warp_push(qt, q, qm, s_lo, E.lo);
-            warp_push(qt, q, qm, s_hi, E.hi);
+            // roots: frontier (insert) or evicted (delete) constrained endpoints
+            push_vertex<MODE == 0>(C, P, s_lo, E.lo, P.op == 0 ? 0 : 1);
+            push_vertex<MODE == 0>(C, P, s_hi, E.hi, P.op == 0 ? 0 : 1);
         }
         if (!(ok = sync(PH_APPLY))) break;
         nrem_next = vload64(&C->spc[1]);
@@ -487,30 +586,43 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         elo = eq0;
         ehi = eq_t;
       }
+      const bool resumed = mid;
       mid = false;
 
         if (P.op == 0) {
-            // -------------------------------------------- SEARCH (insert): frontier + evictions per wave
-            while (fhi > flo || ehi > elo || (MODE == 0 && hubs_pending())) {
-                if (MODE == 1 && (fhi - flo) + (ehi - elo) > (unsigned long long)P.big_wave) {
-                    escalate = true;   // this wave is too big for one block: hand it to the grid
-                    break;
+            // -------------------------------------------- SEARCH (insert): frontier + evictions
+            if (MODE == 0) {
+                if (resumed) {   // the single-block mode began this search
+                    reset_tasks();
+                    if (!(ok = sync(PH_APPLY))) break;
+                    seed_tasks(C, P, P.VQ, flo, fhi, T_FRONT);
+                    seed_tasks(C, P, P.EQ, elo, ehi, T_EVICT);
+                    if (!(ok = sync(PH_APPLY))) break;
                 }
                 waves++;
-                for_each_vertex<MODE, HUB_FRONT>(g, C, P, &C->pc[2], P.VQ, qm, flo, fhi,
-                                                 [&](int v, auto grp) {
-                                                     process_frontier<decltype(grp)>(g, C, P, v, e, ls);
-                                                 });
-                for_each_vertex<MODE, HUB_EVICT_INS>(g, C, P, &C->pc[3], P.EQ, qm, elo, ehi,
-                                                     [&](int v, auto grp) {
-                                                         evict_insert_vertex<decltype(grp)>(g, C, P, v, e, ls);
-                                                     });
-                if (MODE == 0) hub_chunks(g, C, P, e, ls);
-                if (!(ok = sync(PH_DISCOVER))) break;
-                flo = fhi;
+                ok = async_search(g, C, P, e, ls);
+                if (!(ok = sync(PH_DISCOVER) && ok)) break;
                 fhi = vload64(&C->stail[0]);
-                elo = ehi;
                 ehi = vload64(&C->stail[1]);
+            } else {
+                while (fhi > flo || ehi > elo) {
+                    if ((fhi - flo) + (ehi - elo) > (unsigned long long)P.big_wave) {
+                        escalate = true;   // this wave is too big for one block: hand it to the grid
+                        break;
+                    }
+                    waves++;
+                    for_each_vertex<MODE>(g, P, &C->pc[2], P.VQ, qm, flo, fhi, [&](int v, auto grp) {
+                        process_frontier<decltype(grp), false>(g, C, P, v, e, ls);
+                    });
+                    for_each_vertex<MODE>(g, P, &C->pc[3], P.EQ, qm, elo, ehi, [&](int v, auto grp) {
+                        evict_insert_vertex<decltype(grp), false>(g, C, P, v, e, ls);
+                    });
+                    if (!(ok = sync(PH_DISCOVER))) break;
+                    flo = fhi;
+                    fhi = vload64(&C->stail[0]);
+                    elo = ehi;
+                    ehi = vload64(&C->stail[1]);
+                }
             }
             if (!ok || escalate) break;
             vq_t = fhi;
@@ -538,20 +650,31 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             fx_hi = cq_t;
         } else {
             // -------------------------------------------- EVICT (delete); evicted vertices drop by one
-            while (ehi > elo || (MODE == 0 && hubs_pending())) {
-                if (MODE == 1 && ehi - elo > (unsigned long long)P.big_wave) {
-                    escalate = true;
-                    break;
+            if (MODE == 0) {
+                if (resumed) {
+                    reset_tasks();
+                    if (!(ok = sync(PH_APPLY))) break;
+                    seed_tasks(C, P, P.EQ, elo, ehi, T_EVICT);
+                    if (!(ok = sync(PH_APPLY))) break;
                 }
                 waves++;
-                for_each_vertex<MODE, HUB_EVICT_DEL>(g, C, P, &C->pc[2], P.EQ, qm, elo, ehi,
-                                                     [&](int v, auto grp) {
-                                                         evict_delete_vertex<decltype(grp)>(g, C, P, v, e, ls);
-                                                     });
-                if (MODE == 0) hub_chunks(g, C, P, e, ls);
-                if (!(ok = sync(PH_EVICT))) break;
-                elo = ehi;
+                ok = async_search(g, C, P, e, ls);
+                if (!(ok = sync(PH_EVICT) && ok)) break;
                 ehi = vload64(&C->stail[1]);
+            } else {
+                while (ehi > elo) {
+                    if (ehi - elo > (unsigned long long)P.big_wave) {
+                        escalate = true;
+                        break;
+                    }
+                    waves++;
+                    for_each_vertex<MODE>(g, P, &C->pc[2], P.EQ, qm, elo, ehi, [&](int v, auto grp) {
+                        evict_delete_vertex<decltype(grp), false>(g, C, P, v, e, ls);
+                    });
+                    if (!(ok = sync(PH_EVICT))) break;
+                    elo = ehi;
+                    ehi = vload64(&C->stail[1]);
+                }
             }
             if (!ok || escalate) break;
             eq_t = ehi;
@@ -583,7 +706,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         }
     }
     if (ok && fx) {
-        for_each_vertex<MODE, -1>(g, C, P, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
+        for_each_vertex<MODE>(g, P, &C->pc[2], FXQ, qm, fx_lo, fx_hi, fixup_body);
         ok = sync(PH_FIXUP);
     }
     // statistics: one atomic per warp

@@ -33,8 +33,9 @@ struct MaintainParams {
     long long small_work;     // ... and the last iteration touched at most this many items
     long long big_work;       // block -> grid mode when an iteration touches more
     long long big_wave;       // block -> grid mode, inside an iteration, before a wave this large
-    HubItem* HQ;              // hub items of the current wave (ring of kHubRing)
-    HubItem* PQ;              // expansion items (ring of kHubRing)
+    HubItem* HQ;              // hub items of the current search (ring of kHubRing)
+    unsigned long long* TQ;   // grid-mode task queue (ring, TASK_EMPTY when free)
+    unsigned long long tqmask;
     int32_t hub_len;          // grid mode: vertices with at least this many slots are scanned grid-wide
     int32_t block_len;        // vertices with at least this many slots are scanned by a whole block
     int32_t use_cond;         // inside a captured step: the single-block kernel drives the loop node

@@ -114,6 +114,53 @@ struct BlockGroup {
     }
 };
 
+// ---------------------------------------------------------------- queue pushes
+// A vertex that enters the frontier (insert) or is evicted goes to the
+// visited log VQ / evicted log EQ of the iteration.  In the grid-wide mode
+// (ASYNC) it also becomes a task of the iteration's task queue, which warps
+// drain without level barriers (cm_iterate.cu).  All 32 lanes call these.
+constexpr unsigned long long TASK_EMPTY = ~0ull;
+enum { T_FRONT = 0, T_EVICT = 1, T_CHUNK = 2 };
+constexpr int kTaskChunkBits = 22;          // chunk index within a hub item
+constexpr unsigned long long kTaskMargin = 1ull << 16;   // slots kept free for claims past the tail
+
+__device__ __forceinline__ unsigned long long mk_task(int type, unsigned long long payload) {
+    return ((unsigned long long)type << 62) | payload;
+}
+
+// Appends tasks [tb, tb + n) (already reserved); false if the queue is full.
+__device__ __forceinline__ bool task_room(Ctl* C, const MaintainParams& P, unsigned long long tb, unsigned long long n) {
+    if (tb + n + kTaskMargin > P.tqmask + 1) {
+        atomicCAS(&C->error, 0, E_CAPACITY);
+        return false;
+    }
+    return true;
+}
+
+template <bool ASYNC>
+__device__ __forceinline__ void push_vertex(Ctl* C, const MaintainParams& P, bool pred, int32_t v, int which) {
+    // which 0: frontier (VQ, T_FRONT), 1: eviction (EQ, T_EVICT)
+    const unsigned int b = __ballot_sync(0xffffffffu, pred);
+    if (!b) return;
+    const int lane = lane_id();
+    const int leader = __ffs(b) - 1;
+    const unsigned long long cnt = (unsigned long long)__popc(b);
+    unsigned long long lb = 0, tb = 0;
+    if (lane == leader) {
+        lb = atomicAdd(&C->tail[which], cnt);
+        if (ASYNC) tb = atomicAdd(&C->task_tail, cnt);
+    }
+    lb = __shfl_sync(0xffffffffu, lb, leader);
+    const unsigned int rank = __popc(b & ((1u << lane) - 1));
+    int32_t* log = which == 0 ? P.VQ : P.EQ;
+    if (pred) log[(lb + rank) & P.qmask] = v;
+    if (ASYNC) {
+        tb = __shfl_sync(0xffffffffu, tb, leader);
+        if (task_room(C, P, tb, cnt) && pred)
+            vstore64(&P.TQ[(tb + rank) & P.tqmask], mk_task(which == 0 ? T_FRONT : T_EVICT, (unsigned long long)v));
+    }
+}
+
 // Four neighbour ids of this lane for the step starting at `base` (HOLE for
 // slots at or past len).
 __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, int t0, int w[4]) {
@@ -156,7 +203,7 @@ __device__ __forceinline__ int csd_part(const DevGraph& g, int k, long long o, i
 
 // Visits the unvisited core-k neighbours with SD > k in the range and
 // appends them to the next frontier.
-template <class Grp>
+template <class Grp, bool ASYNC>
 __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k, long long o,
                                              int s0, int s1, uint32_t e) {
     SCAN4_RANGE(Grp, s0, s1)
@@ -169,7 +216,7 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
         for (int q = 0; q < 4; q++) {
             bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
             bool p = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
-            warp_push(&C->tail[0], P.VQ, P.qmask, p, w[q]);
+            push_vertex<ASYNC>(C, P, p, w[q], 0);
         }
     SCAN4_END
 }
@@ -177,7 +224,7 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
 // InsertRemove over the range (Algorithm 4): every core-k neighbour with
 // SD > k (visited or not) loses one support; a processed one whose support
 // falls to k leaves too.
-template <class Grp>
+template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
                                                 long long o, int s0, int s1, uint32_t e) {
     SCAN4_RANGE(Grp, s0, s1)
@@ -196,7 +243,7 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
                 add_word(g, C, w[q], e, -1, 0u, of, oc, word_of(h[q]));
                 p = (of & kProcessed) && oc == k + 1;
             }
-            warp_push(&C->tail[1], P.EQ, P.qmask, p, w[q]);
+            push_vertex<ASYNC>(C, P, p, w[q], 1);
         }
     SCAN4_END
 }
@@ -204,7 +251,7 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
 // DeleteRemove over the range (Algorithm 7): each core-k neighbour w loses
 // one support (initially SD(w)) and leaves when it falls below k, i.e. when
 // its count of evicted neighbours reaches SD(w) - k + 1.
-template <class Grp>
+template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
                                                 long long o, int s0, int s1, uint32_t e) {
     SCAN4_RANGE(Grp, s0, s1)
@@ -231,7 +278,7 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
                 p = oc + 1 == thr;
                 if (p) g.chg[w[q]] = e;
             }
-            warp_push(&C->tail[1], P.EQ, P.qmask, p, w[q]);
+            push_vertex<ASYNC>(C, P, p, w[q], 1);
         }
     SCAN4_END
 }
@@ -240,7 +287,7 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
 // Positive search step (Algorithm 3) for a frontier vertex v at level k:
 // support += CSD(v); above k -> visit the unvisited core-k neighbours with
 // SD > k, else v is evicted.
-template <class Grp>
+template <class Grp, bool ASYNC>
 __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
                                                  uint32_t e, LocalStats& ls) {
     const int lane = lane_id();
@@ -263,18 +310,18 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
         sup = Grp::sum(Grp::rank0() ? sup : 0);
     }
     if (sup > k) {
-        expand_range<Grp>(g, C, P, k, o, 0, len, e);
+        expand_range<Grp, ASYNC>(g, C, P, k, o, 0, len, e);
     } else if (Grp::warp0()) {
-        warp_push(&C->tail[1], P.EQ, P.qmask, lane == 0, v);
+        push_vertex<ASYNC>(C, P, lane == 0, v, 1);
     }
 }
 
 // InsertRemove step (Algorithm 4) for an evicted vertex v.
-template <class Grp>
+template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
                                                     uint32_t e, LocalStats& ls) {
     const int len = g.end[v];
-    evict_ins_range<Grp>(g, C, P, g.hs[v].x, g.off[v], 0, len, e);
+    evict_ins_range<Grp, ASYNC>(g, C, P, g.hs[v].x, g.off[v], 0, len, e);
     if (Grp::rank0()) {
         ls.ev++;
         ls.evl += len;
@@ -282,12 +329,12 @@ __device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, c
 }
 
 // DeleteRemove step (Algorithm 7) for an evicted vertex v, which drops to k-1.
-template <class Grp>
+template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
                                                     uint32_t e, LocalStats& ls) {
     const int k = g.hs[v].x;
     const int len = g.end[v];
-    evict_del_range<Grp>(g, C, P, k, g.off[v], 0, len, e);
+    evict_del_range<Grp, ASYNC>(g, C, P, k, g.off[v], 0, len, e);
     if constexpr (Grp::G > 32) __syncthreads();   // every warp has read k before it changes
     if (Grp::rank0()) {
         g.hs[v].x = k - 1;
