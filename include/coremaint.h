@@ -163,8 +163,13 @@ int cm_insert_vertex(cm_graph* g, const int32_t* nbrs, int32_t d, int32_t* new_i
 /* Vertex deletion (Section I): deletes every edge incident to the given
  * live vertices (host or device, count int32; repeats allowed) as one
  * batch, then marks them dead: they keep their ids, report core -1 and
- * reject later edges.  n_applied: edges deleted.  Errors: CM_ERR_INVALID
- * (id out of range or already dead; nothing changed). */
+ * reject later edges.  While their edges go, the deleted vertices are
+ * pinned (their cores stay fixed, so they constrain no edge and never
+ * drop): Definition 6 then only limits the other endpoints, and a deleted
+ * hub loses all its edges in one iteration instead of one per iteration.
+ * The other vertices end with the cores of the graph without the deleted
+ * ones.  n_applied: edges deleted.  Errors: CM_ERR_INVALID (id out of range
+ * or already dead; nothing changed). */
 int cm_delete_vertices(cm_graph* g, int32_t count, const int32_t* ids, int64_t* n_applied);
 
 /* One vertex. */

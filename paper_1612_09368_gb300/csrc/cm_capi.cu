@@ -922,6 +922,16 @@ extern "C" int cm_delete_vertices(cm_graph* h, int32_t count, const int32_t* ids
         if ((rc = rd_ctl(h))) break;
         long long k = (long long)h->hctl->gather_n;
         int64_t applied = 0;
+        // The deleted vertices are pinned: their cores stay fixed until they
+        // are marked dead, so they never constrain an edge and never drop.
+        // Each remaining vertex still loses at most one edge per iteration
+        // at its level (Definition 6 for the other endpoints), and once the
+        // last edge of a pinned vertex is gone it supports nobody, so the
+        // other vertices end with the cores of the graph without them;
+        // a hub's edges then go in one iteration instead of one per
+        // iteration.
+        h->launches++;
+        if ((e = pin_vertices(dids, count, g, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "pin"); break; }
         if (k > 0 && (rc = update_device(h, CM_OP_DELETE, h->dbatch, k, &applied, 0, nullptr))) break;
         h->launches++;
         if ((e = mark_dead(dids, count, h->g, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "mark_dead"); break; }

@@ -23,6 +23,10 @@
 namespace cm {
 
 constexpr int32_t HOLE = -1;
+// SD value of a vertex being deleted (a pinned vertex): during the call its
+// core stays fixed, it constrains no edge, it never becomes a root and its
+// support never runs out (see cm_delete_vertices)
+constexpr int32_t PIN_SD = 1 << 30;
 constexpr unsigned long long KEY_EMPTY = 0xFFFFFFFFFFFFFFFFull;
 constexpr unsigned long long KEY_TOMB = 0xFFFFFFFFFFFFFFFEull;
 constexpr unsigned long long CLAIM_FREE = 0xFFFFFFFFFFFFFFFFull;

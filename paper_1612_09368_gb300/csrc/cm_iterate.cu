@@ -350,11 +350,14 @@ __device__ __forceinline__ void seed_tasks(Ctl* C, const MaintainParams& P, cons
     }
 }
 
+// An edge's core number k = min(core(lo), core(hi)) and its constrained
+// endpoints: those whose core is k (Definition 6), except pinned vertices.
 __device__ __forceinline__ void edge_level(const DevGraph& g, const REdge& E, int& k, bool& clo, bool& chi) {
-    int a = g.hs[E.lo].x, b = g.hs[E.hi].x;
-    k = min(a, b);
-    clo = a == k;
-    chi = b == k;
+    const int2 a = *reinterpret_cast<const int2*>(&g.hs[E.lo]);
+    const int2 b = *reinterpret_cast<const int2*>(&g.hs[E.hi]);
+    k = min(a.x, b.x);
+    clo = a.x == k && a.y < PIN_SD;
+    chi = b.x == k && b.y < PIN_SD;
 }
 
 // Selection, claim phase of round r.

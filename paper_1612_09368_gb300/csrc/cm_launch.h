@@ -98,6 +98,7 @@ cudaError_t validate_ids(const int32_t* ids, int32_t count, DevGraph g, Ctl* c, 
 cudaError_t gather_incident(const int32_t* ids, int32_t count, DevGraph g, int32_t* E, long long cap, Ctl* c,
                             cudaStream_t s);
 cudaError_t mark_dead(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s);
+cudaError_t pin_vertices(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s);
 cudaError_t export_cores(DevGraph g, int32_t* out, cudaStream_t s);
 cudaError_t export_edges(DevGraph g, int32_t* out, Ctl* c, cudaStream_t s);
 cudaError_t localize_multi(int32_t* E, long long k, const unsigned long long* kp, const long long* prefix,

@@ -419,6 +419,20 @@ __global__ void mark_dead_kernel(const int32_t* __restrict__ ids, int32_t count,
     g.deg[v] = 0;
 }
 
+// Vertices being deleted keep their core for the rest of the call and count
+// as fixed support for their neighbours while their edges go (PIN_SD).
+__global__ void pin_vertices_kernel(const int32_t* __restrict__ ids, int32_t count, DevGraph g) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    g.hs[ids[i]].y = PIN_SD;
+}
+
+cudaError_t pin_vertices(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    pin_vertices_kernel<<<grid_for(count, 256), 256, 0, s>>>(ids, count, g);
+    return cudaGetLastError();
+}
+
 cudaError_t validate_ids(const int32_t* ids, int32_t count, DevGraph g, Ctl* c, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     validate_ids_kernel<<<grid_for(count, 256), 256, 0, s>>>(ids, count, g, c);

@@ -207,6 +207,35 @@ def test_vertex_insert_delete(cm):
         assert g.cores()[v] == -1
 
 
+def test_vertex_delete_hubs_and_neighbours(cm):
+    """Deleting hubs, hubs that share neighbours, and adjacent vertices in
+    one call: the deleted vertices are pinned while their edges go, so the
+    call needs far fewer iterations than one edge per hub per iteration,
+    and the cores are those of the graph without them."""
+    scale = 13
+    n = 1 << scale
+    e = synth.rmat(scale, 16, synth.stream(44))
+    g = cm.CoreGraph(n, _dev(e))
+    deg = np.bincount(e.ravel(), minlength=n)
+    hubs = np.argsort(-deg)[:6]
+    nb = e[e[:, 0] == hubs[0], 1][:3]                      # neighbours of the largest hub
+    dead = np.unique(np.concatenate([hubs, nb, [7, 8, 9]])).astype(np.int32)
+    got = g.delete_vertices(dead)
+    keep = ~np.isin(e, dead).any(1)
+    assert got == int((~keep).sum())
+    exp = oracle.bz(n, e[keep])
+    c = g.cores()
+    assert (c[dead] == -1).all()
+    alive = np.setdiff1d(np.arange(n), dead)
+    assert (c[alive] == exp[alive]).all()
+    assert g.stats()["iterations"] < deg[hubs[0]] // 4
+    # the graph keeps working after it
+    ref = oracle.OracleGraph(n, e[keep], mode=oracle.SUPERIOR)
+    dl = synth.static_sample_delete(n, e[keep], 2000, synth.PREFERENTIAL, synth.stream(45))
+    assert g.delete_edges(_dev(dl)) == ref.delete_edges(dl)
+    assert (g.cores()[alive] == ref.cores()[alive]).all()
+
+
 # ---------------------------------------------------------------- edge cases
 def test_edge_cases(cm):
     n = 40
