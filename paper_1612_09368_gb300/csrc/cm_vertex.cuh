@@ -161,6 +161,44 @@ __device__ __forceinline__ void push_vertex(Ctl* C, const MaintainParams& P, boo
     }
 }
 
+// The same for up to four vertices per lane (one scan step), with one
+// atomic per queue for the whole warp.
+template <bool ASYNC>
+__device__ __forceinline__ void push_vertex4(Ctl* C, const MaintainParams& P, const bool pred[4], const int32_t v[4],
+                                             int which) {
+    const int lane = lane_id();
+    const int mine = (int)pred[0] + (int)pred[1] + (int)pred[2] + (int)pred[3];
+    if (!__any_sync(0xffffffffu, mine != 0)) return;
+    int incl = mine;   // inclusive prefix over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const unsigned long long total = (unsigned long long)__shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long lb = 0, tb = 0;
+    if (lane == 31) {
+        lb = atomicAdd(&C->tail[which], total);
+        if (ASYNC) tb = atomicAdd(&C->task_tail, total);
+    }
+    lb = __shfl_sync(0xffffffffu, lb, 31);
+    unsigned long long at = (unsigned long long)(incl - mine);
+    int32_t* log = which == 0 ? P.VQ : P.EQ;
+    bool room = true;
+    if (ASYNC) {
+        tb = __shfl_sync(0xffffffffu, tb, 31);
+        room = task_room(C, P, tb, total);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (!pred[q]) continue;
+        log[(lb + at) & P.qmask] = v[q];
+        if (ASYNC && room)
+            vstore64(&P.TQ[(tb + at) & P.tqmask], mk_task(which == 0 ? T_FRONT : T_EVICT, (unsigned long long)v[q]));
+        at++;
+    }
+}
+
 // Four neighbour ids of this lane for the step starting at `base` (HOLE for
 // slots at or past len).
 __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, int t0, int w[4]) {
@@ -212,12 +250,13 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
         int4 h[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+        bool p[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
-            bool p = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
-            push_vertex<ASYNC>(C, P, p, w[q], 0);
+            p[q] = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
         }
+        push_vertex4<ASYNC>(C, P, p, w, 0);
     SCAN4_END
 }
 
@@ -233,18 +272,19 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
         int4 h[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+        bool p[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const bool gone = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kProcessed) && h[q].w <= k;
-            bool p = false;
+            p[q] = false;
             if (h[q].x == k && h[q].y > k && !gone) {
                 uint32_t of;
                 int32_t oc;
                 add_word(g, C, w[q], e, -1, 0u, of, oc, word_of(h[q]));
-                p = (of & kProcessed) && oc == k + 1;
+                p[q] = (of & kProcessed) && oc == k + 1;
             }
-            push_vertex<ASYNC>(C, P, p, w[q], 1);
         }
+        push_vertex4<ASYNC>(C, P, p, w, 1);
     SCAN4_END
 }
 
@@ -264,22 +304,23 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
             h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
             c[q] = w[q] >= 0 ? g.chg[w[q]] : 0u;
         }
+        bool p[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int thr = h[q].y - k + 1;
             const bool gone = thr <= 0 || (same_iter((uint32_t)h[q].z, e) && h[q].w >= thr);
-            bool p = false;
+            p[q] = false;
             // evicted vertices (chg == e) are skipped: their cores already
             // dropped, so one that fell from k+1 would pass for level k
             if (h[q].x == k && !gone && c[q] != e) {
                 uint32_t of;
                 int32_t oc;
                 add_word(g, C, w[q], e, 1, 0u, of, oc, word_of(h[q]));
-                p = oc + 1 == thr;
-                if (p) g.chg[w[q]] = e;
+                p[q] = oc + 1 == thr;
+                if (p[q]) g.chg[w[q]] = e;
             }
-            push_vertex<ASYNC>(C, P, p, w[q], 1);
         }
+        push_vertex4<ASYNC>(C, P, p, w, 1);
     SCAN4_END
 }
 
