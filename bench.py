@@ -49,14 +49,26 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("cm_iterate.cu", "cm_vertex.cuh", "cm_common.cuh", "cm_launch.h")
+
+
+def kernel_source_sha() -> str:
+    """Hash of the maintenance kernel's sources (the kernel file and the
+    headers it includes), to tell whether a stored ncu capture is current."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1612_09368_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic():
     """DRAM bytes per launch of the maintenance kernel from the committed ncu
     summary, only if the kernel source is unchanged since it was taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "maintain_traffic.json")) as f:
             t = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1612_09368_gb300", "csrc", "cm_iterate.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != t.get("source_sha"):
+        if kernel_source_sha() != t.get("source_sha"):
             return None
         return t.get("dram_bytes_per_launch")
     except Exception:

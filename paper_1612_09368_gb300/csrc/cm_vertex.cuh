@@ -62,13 +62,26 @@ __device__ __forceinline__ unsigned long long word_of(const int4& h) {
 }
 
 // Adds delta to v's count and low_add to its flag bits (only bits that are
-// clear); returns the previous (flags, count) of iteration e.
+// clear); returns the previous (flags, count) of iteration e.  A word that
+// `seen` shows from an older iteration is restamped and updated by one CAS
+// when nobody else touched it since.
 __device__ __forceinline__ void add_word(const DevGraph& g, Ctl* C, int v, uint32_t e, int32_t delta,
                                          uint32_t low_add, uint32_t& oflags, int32_t& ocount,
                                          unsigned long long seen) {
+    unsigned long long* p = iter_word(g, v);
+    if (!same_iter(wz(seen), e)) {
+        const unsigned long long want =
+            ((unsigned long long)(uint32_t)delta << 32) | (unsigned long long)((e << 2) | low_add);
+        const unsigned long long prev = atomicCAS(p, seen, want);
+        if (prev == seen) {
+            oflags = 0;
+            ocount = 0;
+            return;
+        }
+        seen = prev;
+    }
     make_current(g, C, v, e, seen);
-    unsigned long long old =
-        atomicAdd(iter_word(g, v), ((unsigned long long)(uint32_t)delta << 32) + (unsigned long long)low_add);
+    unsigned long long old = atomicAdd(p, ((unsigned long long)(uint32_t)delta << 32) + (unsigned long long)low_add);
     oflags = wz(old) & 3u;
     ocount = ww(old);
 }
@@ -77,10 +90,17 @@ __device__ __forceinline__ void add_word(const DevGraph& g, Ctl* C, int v, uint3
     add_word(g, C, v, e, delta, low_add, oflags, ocount, vload64(iter_word(g, v)));
 }
 
-// Marks v visited in iteration e; true if this call did it.
+// Marks v visited in iteration e; true if this call did it (one CAS when the
+// word is still the older one `seen` shows).
 __device__ __forceinline__ bool visit(const DevGraph& g, Ctl* C, int v, uint32_t e, unsigned long long seen) {
+    unsigned long long* p = iter_word(g, v);
+    if (!same_iter(wz(seen), e)) {
+        const unsigned long long prev = atomicCAS(p, seen, (unsigned long long)((e << 2) | kVisited));
+        if (prev == seen) return true;
+        seen = prev;
+    }
     make_current(g, C, v, e, seen);
-    unsigned long long old = atomicOr(iter_word(g, v), (unsigned long long)kVisited);
+    unsigned long long old = atomicOr(p, (unsigned long long)kVisited);
     return (wz(old) & kVisited) == 0;
 }
 __device__ __forceinline__ bool visit(const DevGraph& g, Ctl* C, int v, uint32_t e) {
@@ -335,6 +355,41 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
     const int k = g.hs[v].x;
     const long long o = g.off[v];
     const int len = g.end[v];
+    if constexpr (Grp::G == 32) {
+        if (len <= 128) {   // one scan step: CSD and expansion from the same gathers
+            int w[4];
+            load4(g, o, len, lane * 4, w);
+            int4 h[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+            int part = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) part += (h[q].x > k) || (h[q].x == k && h[q].y > k);
+            const int pcd = warp_sum(part);
+            int32_t sup = 0;
+            if (lane == 0) {
+                uint32_t of;
+                int32_t oc;
+                add_word(g, C, v, e, pcd, kProcessed, of, oc);
+                sup = oc + pcd;
+                ls.vis++;
+                ls.visl += len;
+            }
+            sup = __shfl_sync(0xffffffffu, sup, 0);
+            if (sup > k) {
+                bool p[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
+                    p[q] = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
+                }
+                push_vertex4<ASYNC>(C, P, p, w, 0);
+            } else {
+                push_vertex<ASYNC>(C, P, lane == 0, v, 1);
+            }
+            return;
+        }
+    }
     const int pcd = Grp::sum(csd_part<Grp>(g, k, o, 0, len));
     int32_t sup = 0;
     if (Grp::rank0()) {
