@@ -77,17 +77,16 @@ struct Resume {
     unsigned long long vq0, eq0, cq0, flo, fhi, elo, ehi;
 };
 
-constexpr int kTails = 6;
+constexpr int kTails = 4;
 
 // A vertex whose adjacency is scanned by all warps of a grid-mode launch,
-// in chunks of kChunk slots (48 bytes; the lists are rings of kHubRing).
+// in chunk tasks of kChunk slots (32 bytes; a ring of kHubRing per handle).
 // kind: HUB_FRONT (insert frontier: chunks sum CSD, the last one decides),
 // HUB_EVICT_INS / HUB_EVICT_DEL (eviction scans), HUB_EXPAND (visit the
 // frontier neighbours of a hub whose support stayed above k).
 enum { HUB_FRONT = 0, HUB_EVICT_INS = 1, HUB_EVICT_DEL = 2, HUB_EXPAND = 3 };
 struct __align__(16) HubItem {
     long long off;                 // adjacency offset
-    unsigned long long c0;         // first chunk (global chunk numbering of its list)
     int32_t v, kind, k, len;
     int32_t nch;                   // chunks
     int32_t acc;                   // partial-sum accumulator (HUB_FRONT)
@@ -105,13 +104,11 @@ struct __align__(128) Ctl {
     unsigned long long release;    // grid barrier: released generation
     int error;                     // first device error (E_*)
     int err_info;
-    // ring tails (monotone in a call): 0 VQ, 1 EQ, 2 CQ, 3 spare, 4 / 5 the
-    // hub and expansion item lists, packed (items << 40 | chunks)
+    // ring tails (monotone in a call): 0 VQ, 1 EQ, 2 CQ, 3 spare
     unsigned long long tail[kTails];
     unsigned long long pc[kTails];     // phase counters, copied to spc and zeroed at every barrier
     unsigned long long stail[kTails];  // snapshot of tail at the last barrier
     unsigned long long spc[kTails];    // snapshot of pc at the last barrier
-    unsigned long long sprev[2];       // stail[4], stail[5] of the barrier before the last
     unsigned long long st[ST_COUNT];
     unsigned long long ph[PH_COUNT];   // nanoseconds per phase (block 0's view)
     // ingest / host exchange
@@ -241,8 +238,6 @@ __device__ __forceinline__ bool grid_sync(Ctl* c, unsigned int expect, unsigned 
         unsigned long long t = atomicAdd(&c->arrive, 1ull);
         unsigned long long gen = t / expect;
         if (t % expect == expect - 1) {
-            c->sprev[0] = c->stail[4];
-            c->sprev[1] = c->stail[5];
             for (int i = 0; i < kTails; i++) {
                 c->stail[i] = vload64(&c->tail[i]);
                 c->spc[i] = vload64(&c->pc[i]);
@@ -275,8 +270,6 @@ __device__ __forceinline__ bool block_sync(Ctl* c) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        c->sprev[0] = c->stail[4];
-        c->sprev[1] = c->stail[5];
         for (int i = 0; i < kTails; i++) {
             c->stail[i] = vload64(&c->tail[i]);
             c->spc[i] = vload64(&c->pc[i]);

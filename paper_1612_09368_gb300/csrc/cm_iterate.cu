@@ -162,7 +162,6 @@ __device__ __forceinline__ bool make_hub(Ctl* C, const MaintainParams& P, int v,
             idx = atomicAdd(&C->hub_created, 1ull);
             HubItem* it = &P.HQ[idx & (kHubRing - 1)];
             it->off = off;
-            it->c0 = 0;
             it->v = v;
             it->kind = kind;
             it->k = k;

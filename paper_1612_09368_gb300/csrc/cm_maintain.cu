@@ -292,7 +292,6 @@ __global__ void phase_maintain_kernel(Ctl* c, StepLog* log, int phase) {
     c->arrive = 0;
     c->release = 0;
     for (int i = 0; i < kTails; i++) c->tail[i] = c->pc[i] = c->stail[i] = c->spc[i] = 0;
-    c->sprev[0] = c->sprev[1] = 0;
     for (int i = 0; i < ST_COUNT; i++) c->st[i] = 0;
     for (int i = 0; i < PH_COUNT; i++) c->ph[i] = 0;
     c->passes = 0;
