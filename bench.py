@@ -193,7 +193,7 @@ def run_reference(args):
     per = []
     total_edges = 0
     total_t = 0.0
-    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    budget = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     for s in range(args.warmup + args.steps):
         rate, edges, t = cpu_oracle_rate(w, budget)
         if s >= args.warmup:
@@ -557,7 +557,7 @@ def synth_uniform(i: int) -> float:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20-rounds", choices=["rmat20-rounds", "rmat24-sweep", "ba512-batched", "serving"])
@@ -597,7 +597,7 @@ def main():
     torch.cuda.set_device(local)
     libbuild.build()
     K, W = args.steps, args.warmup
-    e2e_rounds = 0 if args.no_e2e else K
+    e2e_rounds = 0 if args.no_e2e else min(K, 20)
     w = make_workload(args, W + K + e2e_rounds)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
