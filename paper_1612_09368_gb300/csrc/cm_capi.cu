@@ -728,9 +728,10 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         CK(h, cudaEventRecord(h->ev[3], h->stream));
         if (c.error) {
             h->poisoned = true;
-            const char* why = c.error == E_BARRIER_TIMEOUT ? "a grid barrier wait ran out"
+            const char* why = c.error == E_BARRIER_TIMEOUT ? "a grid barrier or task-queue wait ran out"
                               : c.error == E_ITER_LIMIT   ? "an iteration or retry limit ran out"
                               : c.error == E_CAPACITY     ? "an adjacency list overflowed"
+                              : c.error == E_TASKS        ? "the search task queue ran out of slots"
                                                           : "device error";
             return set_err(h, CM_ERR_LIMIT, "maintenance stopped: %s (code %d)", why, c.error);
         }

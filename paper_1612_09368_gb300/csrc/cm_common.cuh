@@ -37,6 +37,7 @@ constexpr int E_ITER_LIMIT = 2;
 constexpr int E_CAPACITY = 3;
 constexpr int E_INVALID = 4;
 constexpr int E_INDEX_FULL = 5;
+constexpr int E_TASKS = 6;              // the grid-mode task queue ran out of slots
 
 struct __align__(16) Bucket {
     unsigned long long key;

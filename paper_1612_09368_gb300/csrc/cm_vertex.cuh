@@ -151,7 +151,7 @@ __device__ __forceinline__ unsigned long long mk_task(int type, unsigned long lo
 // Appends tasks [tb, tb + n) (already reserved); false if the queue is full.
 __device__ __forceinline__ bool task_room(Ctl* C, const MaintainParams& P, unsigned long long tb, unsigned long long n) {
     if (tb + n + kTaskMargin > P.tqmask + 1) {
-        atomicCAS(&C->error, 0, E_CAPACITY);
+        atomicCAS(&C->error, 0, E_TASKS);
         return false;
     }
     return true;
