@@ -237,6 +237,30 @@ __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, i
 #define SCAN4_BEGIN(Grp, len) SCAN4_RANGE(Grp, 0, len)
 #define SCAN4_END }
 
+// The same walk with the list read two steps ahead: each lane loads the
+// 16-byte words of two consecutive steps before the first step's gathers,
+// so a step's neighbour gathers do not wait behind its own list read.
+// Inside, `int w[4]` holds the step's four neighbour ids (HOLE past s1).
+#define SCANP_RANGE(Grp, o, s0, s1)                                                              \
+    for (int blk_ = (s0) + Grp::first() * 4; blk_ < (s1); blk_ += Grp::G * 8) {                  \
+        int4 A_[2];                                                                               \
+        _Pragma("unroll") for (int j_ = 0; j_ < 2; j_++) {                                         \
+            const int t_ = blk_ + j_ * Grp::G * 4 + lane_id() * 4;                                \
+            A_[j_] = t_ < (s1) ? *reinterpret_cast<const int4*>(g.adj + (o) + t_)                 \
+                               : make_int4(HOLE, HOLE, HOLE, HOLE);                               \
+        }                                                                                         \
+        _Pragma("unroll") for (int j_ = 0; j_ < 2; j_++) {                                         \
+            if (blk_ + j_ * Grp::G * 4 >= (s1)) break;                                            \
+            const int t0_ = blk_ + j_ * Grp::G * 4 + lane_id() * 4;                               \
+            int w[4];                                                                             \
+            w[0] = A_[j_].x;                                                                      \
+            w[1] = t0_ + 1 < (s1) ? A_[j_].y : HOLE;                                              \
+            w[2] = t0_ + 2 < (s1) ? A_[j_].z : HOLE;                                              \
+            w[3] = t0_ + 3 < (s1) ? A_[j_].w : HOLE;
+#define SCANP_END \
+        }         \
+    }
+
 // ---------------------------------------------------------------- range scans
 // Each scan covers slots [s0, s1) of the list at offset o of a vertex at
 // level k, so a vertex can be scanned whole by one group or in chunks by
@@ -247,15 +271,13 @@ __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, i
 template <class Grp>
 __device__ __forceinline__ int csd_part(const DevGraph& g, int k, long long o, int s0, int s1) {
     int pcd = 0;
-    SCAN4_RANGE(Grp, s0, s1)
-        int w[4];
-        load4(g, o, s1, t0_, w);
+    SCANP_RANGE(Grp, o, s0, s1)
         int2 h[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? *reinterpret_cast<const int2*>(&g.hs[w[q]]) : make_int2(-1, 0);
 #pragma unroll
         for (int q = 0; q < 4; q++) pcd += (h[q].x > k) || (h[q].x == k && h[q].y > k);
-    SCAN4_END
+    SCANP_END
     return pcd;
 }
 
@@ -264,9 +286,7 @@ __device__ __forceinline__ int csd_part(const DevGraph& g, int k, long long o, i
 template <class Grp, bool ASYNC>
 __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k, long long o,
                                              int s0, int s1, uint32_t e) {
-    SCAN4_RANGE(Grp, s0, s1)
-        int w[4];
-        load4(g, o, s1, t0_, w);
+    SCANP_RANGE(Grp, o, s0, s1)
         int4 h[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
@@ -277,7 +297,7 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
             p[q] = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
         }
         push_vertex4<ASYNC>(C, P, p, w, 0);
-    SCAN4_END
+    SCANP_END
 }
 
 // InsertRemove over the range (Algorithm 4): every core-k neighbour with
@@ -286,9 +306,7 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
 template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
                                                 long long o, int s0, int s1, uint32_t e) {
-    SCAN4_RANGE(Grp, s0, s1)
-        int w[4];
-        load4(g, o, s1, t0_, w);
+    SCANP_RANGE(Grp, o, s0, s1)
         int4 h[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
@@ -305,7 +323,7 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
             }
         }
         push_vertex4<ASYNC>(C, P, p, w, 1);
-    SCAN4_END
+    SCANP_END
 }
 
 // DeleteRemove over the range (Algorithm 7): each core-k neighbour w loses
@@ -314,9 +332,7 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
 template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
                                                 long long o, int s0, int s1, uint32_t e) {
-    SCAN4_RANGE(Grp, s0, s1)
-        int w[4];
-        load4(g, o, s1, t0_, w);
+    SCANP_RANGE(Grp, o, s0, s1)
         int4 h[4];
         uint32_t c[4];
 #pragma unroll
@@ -341,7 +357,7 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
             }
         }
         push_vertex4<ASYNC>(C, P, p, w, 1);
-    SCAN4_END
+    SCANP_END
 }
 
 // ---------------------------------------------------------------- per-vertex phase bodies
