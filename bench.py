@@ -554,13 +554,96 @@ def synth_uniform(i: int) -> float:
     return synth.uniform(synth.stream(5, 0, 0, synth.PARAM), i)
 
 
+def run_study(args):
+    """Sequential against superior-edge-set processing on the paper's
+    synthetic families (Section VII, the scalability experiments): ER, BA
+    and R-MAT graphs of average degree 8 with n = 2^15 ... 2^21; per graph
+    10^4 uniform new edges inserted, then 10^4 uniform existing edges (of
+    the generated graph) deleted.  Per case: the GPU call time and its
+    iterations, the iteration bound of the first iteration (the most batch
+    edges one vertex constrains at its level, from the cores before the
+    batch), and the paper's sequential single-edge traversal (oracle O3,
+    one host core) timed on a prefix of the same batch and extrapolated."""
+    import torch
+    import oracle
+    import synth
+    import paper_1612_09368_gb300 as cm
+    from paper_1612_09368_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    scales = [int(x) for x in args.study_scales.split(",")]
+    k = 10 ** 4
+    rows = []
+
+    def bound(cores, batch):
+        c = cores[batch]
+        lvl = c.min(1)
+        cons = np.concatenate([batch[:, 0][c[:, 0] == lvl], batch[:, 1][c[:, 1] == lvl]])
+        return int(np.bincount(cons).max()) if len(cons) else 0
+
+    def o3_rate(n, e, batch, op, budget):
+        og = oracle.OracleGraph(n, e, mode=oracle.SEQUENTIAL)
+        done, t = 0, 0.0
+        while done < len(batch) and t < budget:
+            part = batch[done: done + max(50, min(2000, done or 50))]
+            t0 = time.perf_counter()
+            (og.insert_edges if op == 0 else og.delete_edges)(part)
+            t += time.perf_counter() - t0
+            done += len(part)
+        return done / t, done
+
+    for fam in ("er", "ba", "rmat"):
+        for sc in scales:
+            n = 1 << sc
+            seed = synth.stream(6, sc, 0, synth.GRAPH) + {"er": 0, "ba": 1, "rmat": 2}[fam]
+            if fam == "er":
+                e = synth.er(n, 4 * n, seed)
+            elif fam == "ba":
+                e = synth.ba(n, 4, seed)
+            else:
+                e = synth.rmat(sc, 4, seed)
+            ins = synth.static_sample_insert(n, e, k, synth.UNIFORM, synth.stream(6, sc, 1, synth.INSERT))
+            dele = synth.static_sample_delete(n, e, k, synth.PREFERENTIAL, synth.stream(6, sc, 1, synth.DELETE))
+            g = cm.CoreGraph(n, torch.from_numpy(e).to(dev))
+            c0 = g.cores()
+            bi = bound(c0, ins)
+            g.insert_edges(torch.from_numpy(ins).to(dev))
+            si = g.stats()
+            bd = bound(g.cores(), dele)
+            g.delete_edges(torch.from_numpy(dele).to(dev))
+            sd = g.stats()
+            g.close()
+            ri, ni = o3_rate(n, e, ins, 0, args.study_budget)
+            rd, nd = o3_rate(n, e, dele, 1, args.study_budget)
+            row = {"family": fam, "n": n, "edges": int(len(e)), "max_core": int(c0.max()),
+                   "insert": {"gpu_ms": si["call_ms"], "iterations": si["iterations"], "first_bound": bi,
+                              "o3_edges_per_s": ri, "o3_sample": ni,
+                              "speedup_vs_o3": (k / ri * 1000.0) / si["call_ms"]},
+                   "delete": {"gpu_ms": sd["call_ms"], "iterations": sd["iterations"], "first_bound": bd,
+                              "o3_edges_per_s": rd, "o3_sample": nd,
+                              "speedup_vs_o3": (k / rd * 1000.0) / sd["call_ms"]}}
+            rows.append(row)
+            print(json.dumps({"study_case": row}), file=sys.stderr, flush=True)
+    line = {"metric": "sequential vs superior-edge-set study (iterations, GPU ms, speedup over the sequential traversal)",
+            "workload": "study", "unit": "ms", "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "study-er-ba-rmat", "average_degree": 8, "updates": k, "scales": scales,
+                       "o3": f"oracle O3 on one host core, prefix of each batch up to {args.study_budget} s, extrapolated"},
+            "study": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20-rounds", choices=["rmat20-rounds", "rmat24-sweep", "ba512-batched", "serving"])
+    ap.add_argument("--workload", default="rmat20-rounds", choices=["rmat20-rounds", "rmat24-sweep", "ba512-batched", "serving", "study"])
+    ap.add_argument("--study-scales", dest="study_scales", default="15,17,19,21")
+    ap.add_argument("--study-budget", dest="study_budget", type=float, default=3.0)
     ap.add_argument("--rates", default="500,1000,2000,4000,8000,16000")
     ap.add_argument("--duration", type=float, default=3.0)
     ap.add_argument("--budget", type=int, default=1 << 30)
@@ -585,6 +668,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "study":
+        return run_study(args)
 
     import torch
     import paper_1612_09368_gb300 as cm
