@@ -635,13 +635,77 @@ def run_study(args):
     return 0
 
 
+def run_paper_experiments(args):
+    """The paper's two efficiency experiments (Section VII, "Performance
+    Evaluation"), on an R-MAT graph standing in for its SNAP graphs:
+    (1) batch size: P% of the graph's edges (P = 3, 6, 9, 12, 15) chosen
+        uniformly are deleted in one call and then inserted back in one
+        call (which restores the graph);
+    (2) core distribution of the updates: for five core numbers K1 < ... <
+        K5 spread over the graph's edge-core distribution, 20% of the edges
+        whose core number (the smaller core of the endpoints) is K are
+        deleted and inserted back.
+    Reported per call: GPU time, time per edge, iterations."""
+    import torch
+    import synth
+    import paper_1612_09368_gb300 as cm
+    from paper_1612_09368_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sc = args.scale
+    n = 1 << sc
+    e = synth.rmat(sc, 16, synth.stream(7, 0, 0, synth.GRAPH))
+    g = cm.CoreGraph(n, torch.from_numpy(e).to(dev))
+    cores = g.cores()
+    rng = np.random.default_rng(7)
+
+    def cycle(sel):
+        b = torch.from_numpy(np.ascontiguousarray(e[sel])).to(dev)
+        out = {}
+        for name, fn in (("delete", g.delete_edges), ("insert", g.insert_edges)):
+            k = fn(b)
+            st = g.stats()
+            out[name] = {"edges": k, "call_ms": st["call_ms"], "us_per_edge": 1000.0 * st["call_ms"] / max(1, k),
+                         "iterations": st["iterations"], "grid_iterations": st["grid_iterations"]}
+        assert (g.cores() == cores).all(), "a delete then re-insert must restore every core"
+        return out
+
+    size_rows = []
+    for pct in (3, 6, 9, 12, 15):
+        sel = rng.choice(len(e), int(len(e) * pct / 100), replace=False)
+        size_rows.append({"percent": pct, **cycle(sel)})
+        print(json.dumps({"size_case": size_rows[-1]}), file=sys.stderr, flush=True)
+    ecore = np.minimum(cores[e[:, 0]], cores[e[:, 1]])
+    levels = np.unique(ecore)
+    picks = levels[np.clip((np.array([0.1, 0.3, 0.5, 0.7, 0.9]) * (len(levels) - 1)).round().astype(int), 0,
+                           len(levels) - 1)]
+    core_rows = []
+    for K in picks:
+        idx = np.nonzero(ecore == K)[0]
+        sel = rng.choice(idx, max(1, int(0.2 * len(idx))), replace=False)
+        core_rows.append({"core": int(K), "edges_at_core": int(len(idx)), **cycle(sel)})
+        print(json.dumps({"core_case": core_rows[-1]}), file=sys.stderr, flush=True)
+    g.close()
+    line = {"metric": "paper experiments: time per edge and iterations by batch size and by edge core number",
+            "workload": "paper-experiments", "unit": "us/edge", "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"rmat{sc}-paper-experiments", "scale": sc, "edge_factor": 16,
+                       "vertices": n, "edges": int(len(e)), "max_core": int(cores.max()),
+                       "note": "R-MAT stands in for the paper's SNAP graphs; every case deletes then re-inserts"},
+            "batch_size": size_rows, "core_distribution": core_rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20-rounds", choices=["rmat20-rounds", "rmat24-sweep", "ba512-batched", "serving", "study"])
+    ap.add_argument("--workload", default="rmat20-rounds", choices=["rmat20-rounds", "rmat24-sweep", "ba512-batched", "serving", "study",
+                                                              "paper-experiments"])
     ap.add_argument("--study-scales", dest="study_scales", default="15,17,19,21")
     ap.add_argument("--study-budget", dest="study_budget", type=float, default=3.0)
     ap.add_argument("--rates", default="500,1000,2000,4000,8000,16000")
@@ -670,6 +734,8 @@ def main():
         return run_serving(args)
     if args.workload == "study":
         return run_study(args)
+    if args.workload == "paper-experiments":
+        return run_paper_experiments(args)
 
     import torch
     import paper_1612_09368_gb300 as cm

@@ -683,6 +683,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         p.small_work = h->small_work;
         p.big_work = h->big_work;
         p.big_wave = h->big_work / 8 > 64 ? h->big_work / 8 : 64;
+        p.big_slots = 4 * p.big_work;
         if ((rc = ensure_tasks(h))) return rc;
         p.HQ = h->HQ;
         p.TQ = h->TQ;
@@ -1241,6 +1242,7 @@ static MaintainParams step_params(const cm_step* s, int op, int* blocks, int* th
     p.small_work = c.block_mode_enter > 0 ? c.block_mode_enter : 1024;
     p.big_work = c.block_mode_leave > 0 ? c.block_mode_leave : 8192;
     p.big_wave = p.big_work / 8 > 64 ? p.big_work / 8 : 64;
+    p.big_slots = 4 * p.big_work;
     p.HQ = h->HQ;
     p.TQ = h->TQ;
     p.tqmask = h->tq_size - 1;

@@ -127,6 +127,25 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, const Maintai
     }
 }
 
+// Single-block mode: adjacency slots of the vertices of ring ranges
+// [lo0, hi0) and [lo1, hi1) (a wave about to run), summed by the block.
+__device__ __forceinline__ long long wave_slots(const DevGraph& g, const int32_t* r0, unsigned long long lo0,
+                                                unsigned long long hi0, const int32_t* r1, unsigned long long lo1,
+                                                unsigned long long hi1, unsigned long long qm) {
+    __shared__ long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+    long long part = 0;
+    for (unsigned long long i = lo0 + threadIdx.x; i < hi0; i += blockDim.x) part += g.end[r0[i & qm]];
+    for (unsigned long long i = lo1 + threadIdx.x; i < hi1; i += blockDim.x) part += g.end[r1[i & qm]];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane_id() == 0 && part) atomicAdd((unsigned long long*)&s_sum, (unsigned long long)part);
+    __syncthreads();
+    const long long total = s_sum;
+    __syncthreads();
+    return total;
+}
+
 // ---------------------------------------------------------------- grid-mode task queue
 // In grid mode the search of an iteration (insert: positive search and
 // evictions; delete: evictions) runs without level barriers.  Every vertex
@@ -608,8 +627,11 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                 ehi = vload64(&C->stail[1]);
             } else {
                 while (fhi > flo || ehi > elo) {
-                    if ((fhi - flo) + (ehi - elo) > (unsigned long long)P.big_wave) {
-                        escalate = true;   // this wave is too big for one block: hand it to the grid
+                    // a wave too big for one block (by vertices, or by the slots
+                    // of its vertices' lists) goes to the grid
+                    if ((fhi - flo) + (ehi - elo) > (unsigned long long)P.big_wave ||
+                        wave_slots(g, P.VQ, flo, fhi, P.EQ, elo, ehi, qm) > P.big_slots) {
+                        escalate = true;
                         break;
                     }
                     waves++;
@@ -665,7 +687,8 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                 ehi = vload64(&C->stail[1]);
             } else {
                 while (ehi > elo) {
-                    if (ehi - elo > (unsigned long long)P.big_wave) {
+                    if (ehi - elo > (unsigned long long)P.big_wave ||
+                        wave_slots(g, P.EQ, elo, ehi, P.EQ, 0, 0, qm) > P.big_slots) {
                         escalate = true;
                         break;
                     }

@@ -33,6 +33,7 @@ struct MaintainParams {
     long long small_work;     // ... and the last iteration touched at most this many items
     long long big_work;       // block -> grid mode when an iteration touches more
     long long big_wave;       // block -> grid mode, inside an iteration, before a wave this large
+    long long big_slots;      // ... or before a wave whose vertices' lists hold this many slots
     HubItem* HQ;              // hub items of the current search (ring of kHubRing)
     unsigned long long* TQ;   // grid-mode task queue (ring, TASK_EMPTY when free)
     unsigned long long tqmask;
