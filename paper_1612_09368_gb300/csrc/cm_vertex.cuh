@@ -223,7 +223,7 @@ __device__ __forceinline__ void push_vertex4(Ctl* C, const MaintainParams& P, co
 // slots at or past len).
 __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, int t0, int w[4]) {
     int4 a = make_int4(HOLE, HOLE, HOLE, HOLE);
-    if (t0 < len) a = *reinterpret_cast<const int4*>(g.adj + o + t0);
+    if (t0 < len) a = __ldcs(reinterpret_cast<const int4*>(g.adj + o + t0));   // streamed: keep L2 for vertex words
     w[0] = a.x;
     w[1] = t0 + 1 < len ? a.y : HOLE;
     w[2] = t0 + 2 < len ? a.z : HOLE;
@@ -239,14 +239,15 @@ __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, i
 
 // The same walk with the list read two steps ahead: each lane loads the
 // 16-byte words of two consecutive steps before the first step's gathers,
-// so a step's neighbour gathers do not wait behind its own list read.
+// so a step's neighbour gathers do not wait behind its own list read.  List
+// reads are streamed (evict-first) so that L2 keeps the vertex words.
 // Inside, `int w[4]` holds the step's four neighbour ids (HOLE past s1).
 #define SCANP_RANGE(Grp, o, s0, s1)                                                              \
     for (int blk_ = (s0) + Grp::first() * 4; blk_ < (s1); blk_ += Grp::G * 8) {                  \
         int4 A_[2];                                                                               \
         _Pragma("unroll") for (int j_ = 0; j_ < 2; j_++) {                                         \
             const int t_ = blk_ + j_ * Grp::G * 4 + lane_id() * 4;                                \
-            A_[j_] = t_ < (s1) ? *reinterpret_cast<const int4*>(g.adj + (o) + t_)                 \
+            A_[j_] = t_ < (s1) ? __ldcs(reinterpret_cast<const int4*>(g.adj + (o) + t_))                 \
                                : make_int4(HOLE, HOLE, HOLE, HOLE);                               \
         }                                                                                         \
         _Pragma("unroll") for (int j_ = 0; j_ < 2; j_++) {                                         \
