@@ -84,6 +84,8 @@ typedef struct cm_options {
     int32_t block_slots;    /* grid mode, insert: a vertex with at least this many slots (below hub_slots)
                                is scanned by a whole block instead of one warp (4096) */
     int32_t block_slots_delete; /* the same for delete calls (1024) */
+    int32_t task_claim;     /* grid mode: most search tasks a warp claims at once (1..8, default 1) */
+    int32_t reserved;
 } cm_options;
 
 /* Test hook: every grid barrier of the next maintenance launch waits for
@@ -266,6 +268,8 @@ typedef struct cm_step_config {
     int32_t hub_slots;         /* frontier granularity: grid-wide chunked scans from this many slots (0 = 1024, -1 never) */
     int32_t blocks_per_sm;     /* block shape of the grid-mode launch: resident 512-thread blocks per SM (0 = max) */
     int32_t block_slots;       /* frontier granularity: block-wide scans from this many slots, insert phase (0 = 4096) */
+    int32_t task_claim;        /* most search tasks a warp claims at once (0 = 1) */
+    int32_t reserved;
 } cm_step_config;
 
 /* max_insert / max_delete: capacity (edges) of the step's two batches.
@@ -298,9 +302,9 @@ typedef struct cm_tune_report {
 } cm_tune_report;
 
 /* Autotuner: times the step's current configuration, then tunes one knob
- * at a time (coordinate descent, 12 candidates): hub_slots in {512, 1024, 4096,
- * never}, block_slots in {256, 1024, 4096}, blocks_per_sm in {1, 2},
- * and three execution-mode threshold sets, each knob keeping the fastest
+ * at a time (coordinate descent, 15 candidates): hub_slots in {512, 1024, 4096,
+ * never}, block_slots in {256, 1024, 4096}, blocks_per_sm in {1, 2}, three
+ * execution-mode threshold sets and task_claim in {1, 2, 8}, each knob keeping the fastest
  * value with the others at the best found so far.  Each candidate is timed
  * on the given batches, `reps` replays (median), restoring the graph's
  * device state and the batch before every replay; the fastest is kept on

@@ -52,6 +52,7 @@ class cm_options(ctypes.Structure):
         ("spin_limit_ns", ctypes.c_int64), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("debug_flags", ctypes.c_int32), ("block_mode_enter", ctypes.c_int32), ("block_mode_leave", ctypes.c_int32),
         ("hub_slots", ctypes.c_int32), ("block_slots", ctypes.c_int32), ("block_slots_delete", ctypes.c_int32),
+        ("task_claim", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -73,10 +74,11 @@ class cm_stats(ctypes.Structure):
 
 class cm_step_config(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in (
-        "block_mode_edges", "block_mode_enter", "block_mode_leave", "hub_slots", "blocks_per_sm", "block_slots")]
+        "block_mode_edges", "block_mode_enter", "block_mode_leave", "hub_slots", "blocks_per_sm", "block_slots",
+        "task_claim", "reserved")]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class cm_tune_report(ctypes.Structure):

@@ -71,6 +71,7 @@ struct cm_graph {
     unsigned long long tq_size = 0;
     int32_t hub_len = 1024;
     int32_t block_len = 4096, block_len_del = 1024;
+    int32_t claim_max = 1;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -352,6 +353,7 @@ extern "C" void cm_default_options(cm_options* o) {
     o->hub_slots = 1024;
     o->block_slots = 4096;
     o->block_slots_delete = 1024;
+    o->task_claim = 1;
 }
 
 static void free_all(cm_graph* h) {
@@ -471,6 +473,7 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
                                       : h->opt.hub_slots < 0 ? 0 : 1024;
     h->block_len = h->opt.block_slots >= 32 ? h->opt.block_slots : 4096;
     h->block_len_del = h->opt.block_slots_delete >= 32 ? h->opt.block_slots_delete : 1024;
+    h->claim_max = h->opt.task_claim >= 1 && h->opt.task_claim <= 8 ? h->opt.task_claim : 1;
     CK(h, cudaGetDevice(&h->device));
     CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     int coop = 0;
@@ -690,6 +693,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         p.tqmask = h->tq_size - 1;
         p.hub_len = h->hub_len;
         p.block_len = op == CM_OP_INSERT ? h->block_len : h->block_len_del;
+        p.claim_max = h->claim_max;
         int blocks, threads;
         persistent_geometry(h, 0, nrem0, &blocks, &threads);
         p.expect = (uint32_t)blocks;
@@ -1190,6 +1194,7 @@ static void step_default_config(const cm_graph* h, cm_step_config* c) {
     c->hub_slots = h->hub_len > 0 ? h->hub_len : -1;
     c->blocks_per_sm = 0;
     c->block_slots = h->block_len;
+    c->task_claim = h->claim_max;
 }
 
 static StepSig step_signature(const cm_step* s) {
@@ -1248,6 +1253,7 @@ static MaintainParams step_params(const cm_step* s, int op, int* blocks, int* th
     p.tqmask = h->tq_size - 1;
     p.hub_len = c.hub_slots > 0 ? (c.hub_slots < 128 ? 128 : c.hub_slots) : c.hub_slots < 0 ? 0 : 1024;
     p.block_len = op == CM_OP_INSERT ? (c.block_slots >= 32 ? c.block_slots : 4096) : h->block_len_del;
+    p.claim_max = c.task_claim >= 1 && c.task_claim <= 8 ? c.task_claim : 1;
     int occ = maintain_blocks_per_sm(kGridThreadsHost);
     if (occ < 1) occ = 1;
     int bps = c.blocks_per_sm > 0 && c.blocks_per_sm < occ ? c.blocks_per_sm : occ;
@@ -1789,7 +1795,8 @@ extern "C" int cm_step_autotune(cm_step* s, const int64_t* ins_counts, const int
     const int32_t blocks[] = {256, 1024, 4096};
     const int32_t bps[] = {1, 2};
     const int32_t modes[][3] = {{16384, 1024, 8192}, {65536, 4096, 32768}, {-1, 1024, 8192}};
-    for (int knob = 0; knob < 4 && rc == CM_OK; knob++) {
+    const int32_t claims[] = {1, 2, 8};
+    for (int knob = 0; knob < 5 && rc == CM_OK; knob++) {
         const int nv = knob == 0 ? 4 : knob == 1 ? 3 : knob == 2 ? 2 : 3;
         cm_step_config base = best;
         for (int v = 0; v < nv && rc == CM_OK; v++) {
@@ -1797,6 +1804,7 @@ extern "C" int cm_step_autotune(cm_step* s, const int64_t* ins_counts, const int
             if (knob == 0) c.hub_slots = hubs[v];
             else if (knob == 1) c.block_slots = blocks[v];
             else if (knob == 2) c.blocks_per_sm = bps[v];
+            else if (knob == 4) c.task_claim = claims[v];
             else {
                 c.block_mode_edges = modes[v][0];
                 c.block_mode_enter = modes[v][1];

@@ -260,13 +260,14 @@ __device__ __forceinline__ void run_chunk(const DevGraph& g, Ctl* C, const Maint
 }
 
 // Drains the task queue (every warp of the grid).  Returns false on error.
-// A warp claims up to kClaim consecutive slots with one atomic -- it doubles
-// its claim while its slots are ready at once and drops back to one slot
-// after it had to wait, so small searches keep every warp busy and large
-// ones touch the shared head counter less -- and reports its finished tasks
-// in batches, always before it waits on an empty slot (so a waiting warp
-// never holds back the quiescence test).
-constexpr int kClaim = 8;
+// A warp claims up to P.claim_max consecutive slots with one atomic: it
+// doubles its claim while its slots are ready at once and drops back to one
+// slot after a wait.  One slot at a time balances best when tasks are large
+// (a warp holding a run of large tasks leaves others idle); several save
+// head-counter traffic when tasks are tiny (the many-graph workload), so the
+// limit is a schedule knob.  Finished tasks are reported in batches, always
+// before the warp waits on an empty slot (so a waiting warp never holds back
+// the quiescence test).
 __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const MaintainParams& P, uint32_t e,
                                           LocalStats& ls) {
     using WG = WarpGroup;
@@ -275,12 +276,13 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
     unsigned long long idx = 0, ndone = 0;
     int left = 0, claim = 1;
     bool waited = false;
+    const int cmax = P.claim_max > 1 ? P.claim_max : 1;
     for (;;) {
         unsigned long long t = TASK_EMPTY;
         int quit = 0;
         if (lane == 0) {
             if (left == 0) {
-                claim = waited ? 1 : min(2 * claim, kClaim);
+                claim = waited ? 1 : min(2 * claim, cmax);
                 waited = false;
                 idx = atomicAdd(&C->task_head, (unsigned long long)claim);
                 left = claim;
@@ -321,8 +323,8 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
         if (__shfl_sync(0xffffffffu, quit, 0)) break;
         t = __shfl_sync(0xffffffffu, t, 0);
         // acquire: the task's vertex data as its producers left it (measured
-        // necessary: without it a warp running consecutive claimed tasks
-        // reached wrong cores on small delete batches)
+        // necessary: without it, warps running several claimed tasks in a
+        // row reached wrong cores on small delete batches)
         __threadfence();
         const int type = (int)(t >> 62);
         const unsigned long long payload = t & ((1ull << 62) - 1);

@@ -39,6 +39,7 @@ struct MaintainParams {
     unsigned long long tqmask;
     int32_t hub_len;          // grid mode: vertices with at least this many slots are scanned grid-wide
     int32_t block_len;        // vertices with at least this many slots are scanned by a whole block
+    int32_t claim_max;        // grid-mode task queue: most slots a warp claims at once
     int32_t use_cond;         // inside a captured step: the single-block kernel drives the loop node
     unsigned long long cond;  // that node's conditional handle
 };

@@ -176,7 +176,7 @@ def test_autotune_leaves_graph_unchanged(cm, stream):
     c0 = g.cores().copy()
     e0 = set(map(tuple, np.sort(g.edges(), 1).tolist()))
     rep = st.autotune(ci, np.concatenate(ins), cd, np.concatenate(dele), reps=1)
-    assert rep["tried"] == 13 and rep["best_ms"] > 0 and rep["best_ms"] <= rep["first_ms"]
+    assert rep["tried"] == 16 and rep["best_ms"] > 0 and rep["best_ms"] <= rep["first_ms"]
     assert (g.cores() == c0).all()
     assert set(map(tuple, np.sort(g.edges(), 1).tolist())) == e0
     assert st.config.as_dict() == rep["best"]
