@@ -63,6 +63,7 @@ namespace cm {
 
 constexpr int kBlockThreads = 512;    // single-block mode
 constexpr int kGridThreads = 512;     // grid mode, per block
+static_assert(kGridThreads / 32 == kGridWarps, "one kept-task slot per grid-mode warp");
 constexpr int kMaxBig = 64;
 constexpr int kBlockLenSingle = 256;   // single-block mode: the block scans lists from this size
 
@@ -239,7 +240,7 @@ __device__ __forceinline__ void run_chunk(const DevGraph& g, Ctl* C, const Maint
         decide = __shfl_sync(0xffffffffu, decide, 0);
         if (decide == 1 && !make_hub(C, P, v, HUB_EXPAND, k, off, len))
             expand_range<WG, true>(g, C, P, k, off, 0, len, e);
-        if (decide == 2) push_vertex<true>(C, P, lane == 0, v, 1);
+        if (decide == 2) push_vertex<true>(C, P, lane == 0, v, 1, true);
         return;
     }
     if (kind == HUB_EXPAND) expand_range<WG, true>(g, C, P, k, off, s0, s1, e);
@@ -277,10 +278,16 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
     int left = 0, claim = 1;
     bool waited = false;
     const int cmax = P.claim_max > 1 ? P.claim_max : 1;
+    if (lane == 0) kept_task() = TASK_EMPTY;
+    __syncwarp();
     for (;;) {
-        unsigned long long t = TASK_EMPTY;
+        unsigned long long t = kept_task();
         int quit = 0;
-        if (lane == 0) {
+        const bool own = t != TASK_EMPTY;   // the task this warp kept from its last one
+        __syncwarp();
+        if (own) {
+            if (lane == 0) kept_task() = TASK_EMPTY;
+        } else if (lane == 0) {
             if (left == 0) {
                 claim = waited ? 1 : min(2 * claim, cmax);
                 waited = false;
@@ -322,6 +329,7 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
         }
         if (__shfl_sync(0xffffffffu, quit, 0)) break;
         t = __shfl_sync(0xffffffffu, t, 0);
+        __syncwarp();
         // acquire: the task's vertex data as its producers left it (measured
         // necessary: without it, warps running several claimed tasks in a
         // row reached wrong cores on small delete batches)
@@ -332,21 +340,23 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
             run_chunk(g, C, P, e, ls, payload);
         } else {
             const int v = (int)payload;
-            const int len = g.end[v];
-            const bool hub = P.hub_len > 0 && len >= P.hub_len;
+            const VInfo vi = load_vinfo(g, v);
+            const bool hub = P.hub_len > 0 && vi.len >= P.hub_len;
             if (type == T_FRONT) {
-                if (!hub || !make_hub(C, P, v, HUB_FRONT, g.hs[v].x, g.off[v], len))
-                    process_frontier<WG, true>(g, C, P, v, e, ls);
+                if (!hub || !make_hub(C, P, v, HUB_FRONT, vi.h.x, vi.o, vi.len))
+                    process_frontier<WG, true>(g, C, P, v, vi, e, ls);
             } else if (P.op == 0) {
-                if (!hub || !make_hub(C, P, v, HUB_EVICT_INS, g.hs[v].x, g.off[v], len))
-                    evict_insert_vertex<WG, true>(g, C, P, v, e, ls);
+                if (!hub || !make_hub(C, P, v, HUB_EVICT_INS, vi.h.x, vi.o, vi.len))
+                    evict_insert_vertex<WG, true>(g, C, P, vi, e, ls);
             } else {
-                if (!hub || !make_hub(C, P, v, HUB_EVICT_DEL, g.hs[v].x, g.off[v], len))
-                    evict_delete_vertex<WG, true>(g, C, P, v, e, ls);
+                if (!hub || !make_hub(C, P, v, HUB_EVICT_DEL, vi.h.x, vi.o, vi.len))
+                    evict_delete_vertex<WG, true>(g, C, P, v, vi, e, ls);
             }
         }
         __syncwarp();
-        if (lane == 0) ndone++;   // this task's pushes precede the fence of the next report
+        // this task's pushes precede the fence of the next report; a kept
+        // task was never counted in the tail
+        if (lane == 0 && !own) ndone++;
     }
     return vload32(&C->error) == 0;
 }
@@ -638,10 +648,10 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                     }
                     waves++;
                     for_each_vertex<MODE>(g, P, &C->pc[2], P.VQ, qm, flo, fhi, [&](int v, auto grp) {
-                        process_frontier<decltype(grp), false>(g, C, P, v, e, ls);
+                        process_frontier<decltype(grp), false>(g, C, P, v, load_vinfo(g, v), e, ls);
                     });
                     for_each_vertex<MODE>(g, P, &C->pc[3], P.EQ, qm, elo, ehi, [&](int v, auto grp) {
-                        evict_insert_vertex<decltype(grp), false>(g, C, P, v, e, ls);
+                        evict_insert_vertex<decltype(grp), false>(g, C, P, load_vinfo(g, v), e, ls);
                     });
                     if (!(ok = sync(PH_DISCOVER))) break;
                     flo = fhi;
@@ -696,7 +706,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                     }
                     waves++;
                     for_each_vertex<MODE>(g, P, &C->pc[2], P.EQ, qm, elo, ehi, [&](int v, auto grp) {
-                        evict_delete_vertex<decltype(grp), false>(g, C, P, v, e, ls);
+                        evict_delete_vertex<decltype(grp), false>(g, C, P, v, load_vinfo(g, v), e, ls);
                     });
                     if (!(ok = sync(PH_EVICT))) break;
                     elo = ehi;

@@ -157,18 +157,35 @@ __device__ __forceinline__ bool task_room(Ctl* C, const MaintainParams& P, unsig
     return true;
 }
 
+// The task a warp keeps for itself (grid mode).  Of the vertices a warp
+// produces in the last scan step of its current task, the first is not
+// queued: the warp runs it next, which saves the hand-off through the queue
+// (the slot write, another warp's poll and its back-off) on every level of a
+// dependency chain, such as a frontier vertex that fails and evicts itself or
+// an eviction that evicts a neighbour.  The kept task is not counted in the
+// queue's tail and is not reported done; the task that produced it is
+// reported only after the warp has run it, so quiescence still waits for it.
+constexpr int kGridWarps = 16;   // warps per grid-mode block
+__shared__ unsigned long long s_keep[kGridWarps];
+__device__ __forceinline__ unsigned long long& kept_task() { return s_keep[threadIdx.x >> 5]; }
+
+// Pushes the vertices of the lanes with pred set (warp-collective).  keep:
+// this is the task's last scan step, so the warp may keep one of them.
 template <bool ASYNC>
-__device__ __forceinline__ void push_vertex(Ctl* C, const MaintainParams& P, bool pred, int32_t v, int which) {
+__device__ __forceinline__ void push_vertex(Ctl* C, const MaintainParams& P, bool pred, int32_t v, int which,
+                                            bool keep = false) {
     // which 0: frontier (VQ, T_FRONT), 1: eviction (EQ, T_EVICT)
     const unsigned int b = __ballot_sync(0xffffffffu, pred);
     if (!b) return;
     const int lane = lane_id();
     const int leader = __ffs(b) - 1;
     const unsigned long long cnt = (unsigned long long)__popc(b);
+    if (ASYNC) keep = keep && kept_task() == TASK_EMPTY;   // the same value in every lane
+    const unsigned long long nq = cnt - (ASYNC && keep ? 1 : 0);
     unsigned long long lb = 0, tb = 0;
     if (lane == leader) {
         lb = atomicAdd(&C->tail[which], cnt);
-        if (ASYNC) tb = atomicAdd(&C->task_tail, cnt);
+        if (ASYNC && nq) tb = atomicAdd(&C->task_tail, nq);
     }
     lb = __shfl_sync(0xffffffffu, lb, leader);
     const unsigned int rank = __popc(b & ((1u << lane) - 1));
@@ -176,8 +193,11 @@ __device__ __forceinline__ void push_vertex(Ctl* C, const MaintainParams& P, boo
     if (pred) log[(lb + rank) & P.qmask] = v;
     if (ASYNC) {
         tb = __shfl_sync(0xffffffffu, tb, leader);
-        if (task_room(C, P, tb, cnt) && pred)
-            vstore64(&P.TQ[(tb + rank) & P.tqmask], mk_task(which == 0 ? T_FRONT : T_EVICT, (unsigned long long)v));
+        const unsigned long long task = mk_task(which == 0 ? T_FRONT : T_EVICT, (unsigned long long)v);
+        const bool room = nq == 0 || task_room(C, P, tb, nq);
+        if (pred && keep && rank == 0) kept_task() = task;
+        else if (pred && room) vstore64(&P.TQ[(tb + rank - (keep ? 1 : 0)) & P.tqmask], task);
+        __syncwarp();
     }
 }
 
@@ -185,7 +205,7 @@ __device__ __forceinline__ void push_vertex(Ctl* C, const MaintainParams& P, boo
 // atomic per queue for the whole warp.
 template <bool ASYNC>
 __device__ __forceinline__ void push_vertex4(Ctl* C, const MaintainParams& P, const bool pred[4], const int32_t v[4],
-                                             int which) {
+                                             int which, bool keep = false) {
     const int lane = lane_id();
     const int mine = (int)pred[0] + (int)pred[1] + (int)pred[2] + (int)pred[3];
     if (!__any_sync(0xffffffffu, mine != 0)) return;
@@ -196,10 +216,12 @@ __device__ __forceinline__ void push_vertex4(Ctl* C, const MaintainParams& P, co
         if (lane >= o) incl += t;
     }
     const unsigned long long total = (unsigned long long)__shfl_sync(0xffffffffu, incl, 31);
+    if (ASYNC) keep = keep && kept_task() == TASK_EMPTY;
+    const unsigned long long nq = total - (ASYNC && keep ? 1 : 0);
     unsigned long long lb = 0, tb = 0;
     if (lane == 31) {
         lb = atomicAdd(&C->tail[which], total);
-        if (ASYNC) tb = atomicAdd(&C->task_tail, total);
+        if (ASYNC && nq) tb = atomicAdd(&C->task_tail, nq);
     }
     lb = __shfl_sync(0xffffffffu, lb, 31);
     unsigned long long at = (unsigned long long)(incl - mine);
@@ -207,16 +229,20 @@ __device__ __forceinline__ void push_vertex4(Ctl* C, const MaintainParams& P, co
     bool room = true;
     if (ASYNC) {
         tb = __shfl_sync(0xffffffffu, tb, 31);
-        room = task_room(C, P, tb, total);
+        room = nq == 0 || task_room(C, P, tb, nq);
     }
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         if (!pred[q]) continue;
         log[(lb + at) & P.qmask] = v[q];
-        if (ASYNC && room)
-            vstore64(&P.TQ[(tb + at) & P.tqmask], mk_task(which == 0 ? T_FRONT : T_EVICT, (unsigned long long)v[q]));
+        if (ASYNC) {
+            const unsigned long long task = mk_task(which == 0 ? T_FRONT : T_EVICT, (unsigned long long)v[q]);
+            if (keep && at == 0) kept_task() = task;
+            else if (room) vstore64(&P.TQ[(tb + at - (keep ? 1 : 0)) & P.tqmask], task);
+        }
         at++;
     }
+    if (ASYNC) __syncwarp();
 }
 
 // Four neighbour ids of this lane for the step starting at `base` (HOLE for
@@ -241,7 +267,8 @@ __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, i
 // 16-byte words of two consecutive steps before the first step's gathers,
 // so a step's neighbour gathers do not wait behind its own list read.  List
 // reads are streamed (evict-first) so that L2 keeps the vertex words.
-// Inside, `int w[4]` holds the step's four neighbour ids (HOLE past s1).
+// Inside, `int w[4]` holds the step's four neighbour ids (HOLE past s1)
+// and `last_` is set in the group's last step.
 #define SCANP_RANGE(Grp, o, s0, s1)                                                              \
     for (int blk_ = (s0) + Grp::first() * 4; blk_ < (s1); blk_ += Grp::G * 8) {                  \
         int4 A_[2];                                                                               \
@@ -253,6 +280,7 @@ __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, i
         _Pragma("unroll") for (int j_ = 0; j_ < 2; j_++) {                                         \
             if (blk_ + j_ * Grp::G * 4 >= (s1)) break;                                            \
             const int t0_ = blk_ + j_ * Grp::G * 4 + lane_id() * 4;                               \
+            const bool last_ = blk_ + (j_ + 1) * Grp::G * 4 >= (s1);                              \
             int w[4];                                                                             \
             w[0] = A_[j_].x;                                                                      \
             w[1] = t0_ + 1 < (s1) ? A_[j_].y : HOLE;                                              \
@@ -297,7 +325,7 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
             bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
             p[q] = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
         }
-        push_vertex4<ASYNC>(C, P, p, w, 0);
+        push_vertex4<ASYNC>(C, P, p, w, 0, last_);
     SCANP_END
 }
 
@@ -323,7 +351,7 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
                 p[q] = (of & kProcessed) && oc == k + 1;
             }
         }
-        push_vertex4<ASYNC>(C, P, p, w, 1);
+        push_vertex4<ASYNC>(C, P, p, w, 1, last_);
     SCANP_END
 }
 
@@ -357,21 +385,36 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
                 if (p[q]) g.chg[w[q]] = e;
             }
         }
-        push_vertex4<ASYNC>(C, P, p, w, 1);
+        push_vertex4<ASYNC>(C, P, p, w, 1, last_);
     SCANP_END
 }
 
 // ---------------------------------------------------------------- per-vertex phase bodies
+// A task's vertex: its 16-byte word, list offset and length, loaded
+// together (three independent loads) before anything uses them.
+struct VInfo {
+    int4 h;
+    long long o;
+    int len;
+};
+__device__ __forceinline__ VInfo load_vinfo(const DevGraph& g, int v) {
+    VInfo r;
+    r.h = g.hs[v];
+    r.o = g.off[v];
+    r.len = g.end[v];
+    return r;
+}
+
 // Positive search step (Algorithm 3) for a frontier vertex v at level k:
 // support += CSD(v); above k -> visit the unvisited core-k neighbours with
 // SD > k, else v is evicted.
 template <class Grp, bool ASYNC>
 __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                 uint32_t e, LocalStats& ls) {
+                                                 const VInfo& vi, uint32_t e, LocalStats& ls) {
     const int lane = lane_id();
-    const int k = g.hs[v].x;
-    const long long o = g.off[v];
-    const int len = g.end[v];
+    const int k = vi.h.x;
+    const long long o = vi.o;
+    const int len = vi.len;
     if constexpr (Grp::G == 32) {
         if (len <= 128) {   // one scan step: CSD and expansion from the same gathers
             int w[4];
@@ -387,7 +430,7 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
             if (lane == 0) {
                 uint32_t of;
                 int32_t oc;
-                add_word(g, C, v, e, pcd, kProcessed, of, oc);
+                add_word(g, C, v, e, pcd, kProcessed, of, oc, word_of(vi.h));
                 sup = oc + pcd;
                 ls.vis++;
                 ls.visl += len;
@@ -400,9 +443,9 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
                     const bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
                     p[q] = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
                 }
-                push_vertex4<ASYNC>(C, P, p, w, 0);
+                push_vertex4<ASYNC>(C, P, p, w, 0, true);
             } else {
-                push_vertex<ASYNC>(C, P, lane == 0, v, 1);
+                push_vertex<ASYNC>(C, P, lane == 0, v, 1, true);
             }
             return;
         }
@@ -412,7 +455,7 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
     if (Grp::rank0()) {
         uint32_t of;
         int32_t oc;
-        add_word(g, C, v, e, pcd, kProcessed, of, oc);
+        add_word(g, C, v, e, pcd, kProcessed, of, oc, word_of(vi.h));
         sup = oc + pcd;
         ls.vis++;
         ls.visl += len;
@@ -425,16 +468,16 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
     if (sup > k) {
         expand_range<Grp, ASYNC>(g, C, P, k, o, 0, len, e);
     } else if (Grp::warp0()) {
-        push_vertex<ASYNC>(C, P, lane == 0, v, 1);
+        push_vertex<ASYNC>(C, P, lane == 0, v, 1, Grp::G == 32);
     }
 }
 
 // InsertRemove step (Algorithm 4) for an evicted vertex v.
 template <class Grp, bool ASYNC>
-__device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                    uint32_t e, LocalStats& ls) {
-    const int len = g.end[v];
-    evict_ins_range<Grp, ASYNC>(g, C, P, g.hs[v].x, g.off[v], 0, len, e);
+__device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P,
+                                                    const VInfo& vi, uint32_t e, LocalStats& ls) {
+    const int len = vi.len;
+    evict_ins_range<Grp, ASYNC>(g, C, P, vi.h.x, vi.o, 0, len, e);
     if (Grp::rank0()) {
         ls.ev++;
         ls.evl += len;
@@ -444,10 +487,10 @@ __device__ __forceinline__ void evict_insert_vertex(const DevGraph& g, Ctl* C, c
 // DeleteRemove step (Algorithm 7) for an evicted vertex v, which drops to k-1.
 template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, const MaintainParams& P, int v,
-                                                    uint32_t e, LocalStats& ls) {
-    const int k = g.hs[v].x;
-    const int len = g.end[v];
-    evict_del_range<Grp, ASYNC>(g, C, P, k, g.off[v], 0, len, e);
+                                                    const VInfo& vi, uint32_t e, LocalStats& ls) {
+    const int k = vi.h.x;
+    const int len = vi.len;
+    evict_del_range<Grp, ASYNC>(g, C, P, k, vi.o, 0, len, e);
     if constexpr (Grp::G > 32) __syncthreads();   // every warp has read k before it changes
     if (Grp::rank0()) {
         g.hs[v].x = k - 1;
