@@ -105,10 +105,12 @@ struct __align__(128) Ctl {
     unsigned long long release;    // grid barrier: released generation
     int error;                     // first device error (E_*)
     int err_info;
-    // ring tails (monotone in a call): 0 VQ, 1 EQ, 2 CQ, 3 spare
-    unsigned long long tail[kTails];
-    unsigned long long pc[kTails];     // phase counters, copied to spc and zeroed at every barrier
-    unsigned long long stail[kTails];  // snapshot of tail at the last barrier
+    // ring tails (monotone in a call): 0 VQ, 1 EQ, 2 CQ, 3 spare.  Counters
+    // that every warp updates during a search sit on lines of their own
+    // (128 bytes apart), so their atomics do not queue behind one another.
+    alignas(128) unsigned long long tail[kTails];
+    alignas(128) unsigned long long pc[kTails];     // phase counters, copied to spc and zeroed at every barrier
+    alignas(128) unsigned long long stail[kTails];  // snapshot of tail at the last barrier
     unsigned long long spc[kTails];    // snapshot of pc at the last barrier
     unsigned long long st[ST_COUNT];
     unsigned long long ph[PH_COUNT];   // nanoseconds per phase (block 0's view)
@@ -123,11 +125,12 @@ struct __align__(128) Ctl {
     int defer;                     // captured step: skip its remaining kernels (1 pool short, 2 error)
     unsigned long long passes;     // captured step: launch pairs of the current phase
     // grid-mode task queue of the current search (reset before each search)
-    unsigned long long task_head;  // next slot a warp claims
-    unsigned long long task_tail;  // slots reserved by producers
-    unsigned long long task_done;  // tasks finished
-    unsigned long long hub_created, hub_finished;   // hub items of the current search
-    Resume rs;
+    alignas(128) unsigned long long task_head;  // next slot a warp claims
+    alignas(128) unsigned long long task_tail;  // slots reserved by producers
+    alignas(128) unsigned long long task_done;  // tasks finished
+    alignas(128) unsigned long long hub_created;    // hub items of the current search
+    unsigned long long hub_finished;
+    alignas(128) Resume rs;
 };
 
 // What a captured update step records per phase (0 insert, 1 delete) for

@@ -260,6 +260,9 @@ __device__ __forceinline__ void run_chunk(const DevGraph& g, Ctl* C, const Maint
     }
 }
 
+// Search (iteration number) whose queue the block's poller found quiescent.
+__shared__ volatile uint32_t s_quiet;
+
 // Drains the task queue (every warp of the grid).  Returns false on error.
 // A warp claims up to P.claim_max consecutive slots with one atomic: it
 // doubles its claim while its slots are ready at once and drops back to one
@@ -278,6 +281,11 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
     int left = 0, claim = 1;
     bool waited = false;
     const int cmax = P.claim_max > 1 ? P.claim_max : 1;
+    // one warp per block tests quiescence and tells the others through
+    // shared memory: a test reads two hot counters, and thousands of
+    // waiting warps reading them would slow the claims and pushes that
+    // share those counters' L2 slices
+    const bool poller = threadIdx.x < 32;
     if (lane == 0) kept_task() = TASK_EMPTY;
     __syncwarp();
     for (;;) {
@@ -308,18 +316,22 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
                     atomicAdd(&C->task_done, ndone);
                     ndone = 0;
                 }
-                if ((spins & 3u) == 0) {
+                if (poller) {
                     // quiescent: every task pushed has finished (done read first)
                     const unsigned long long d = vload64(&C->task_done);
                     if (d == vload64(&C->task_tail) || vload32(&C->error)) {
+                        s_quiet = e;
                         quit = 1;
                         break;
                     }
-                    if (gtimer() - t_start > P.limit_ns) {
-                        atomicCAS(&C->error, 0, E_BARRIER_TIMEOUT);
-                        quit = 1;
-                        break;
-                    }
+                } else if (s_quiet == e) {
+                    quit = 1;
+                    break;
+                }
+                if ((spins & 3u) == 0 && gtimer() - t_start > P.limit_ns) {
+                    atomicCAS(&C->error, 0, E_BARRIER_TIMEOUT);
+                    quit = 1;
+                    break;
                 }
                 __nanosleep(nap);
                 if (nap < 2048) nap <<= 1;
@@ -461,6 +473,10 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     if (done0 || want != MODE || vload32(&C->error)) {
         if (MODE == 1) loop_control(P, C);
         return;
+    }
+    if (MODE == 0) {   // shared memory starts undefined: no search is quiescent yet
+        if (threadIdx.x == 0) s_quiet = ~0u;
+        __syncthreads();
     }
     const int lane = lane_id();
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
