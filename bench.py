@@ -784,6 +784,8 @@ def main():
     per_call_it = {k: [] for k in per_call_ms}
     per_call_grid_it = {k: 0 for k in per_call_ms}
     per_call_bar = {k: 0 for k in per_call_ms}
+    per_call_maint = {k: [] for k in per_call_ms}
+    per_call_launch = {k: 0 for k in per_call_ms}
     per_call_vol = {k: {"visited": 0, "visited_slots": 0, "evicted": 0, "evicted_slots": 0, "changed": 0,
                         "changed_slots": 0, "waves": 0, "select_rounds": 0} for k in per_call_ms}
     phase_ns = {}
@@ -798,6 +800,8 @@ def main():
             per_call_it[name].append(x["iterations"])
             per_call_grid_it[name] += x["grid_iterations"]
             per_call_bar[name] += x["barriers"]
+            per_call_maint[name].append(x["maintain_ms"])
+            per_call_launch[name] += x["launches"]
             for vk in per_call_vol[name]:
                 per_call_vol[name][vk] += x[vk]
             for ph, ns in x["phase_ns"].items():
@@ -890,6 +894,8 @@ def main():
                            "call_ms_median": {k: statistics.median(v) for k, v in per_call_ms.items()},
                            "call_ms_mean": {k: float(np.mean(v)) for k, v in per_call_ms.items()},
                            "iterations_mean": {k: float(np.mean(v)) for k, v in per_call_it.items()},
+                           "maintain_ms_median": {k: statistics.median(v) for k, v in per_call_maint.items()},
+                           "launches_per_call": {k: v / K for k, v in per_call_launch.items()},
                            "grid_iterations": per_call_grid_it, "barriers": per_call_bar,
                            "volumes": per_call_vol,
                            "phase_ms": {k: v / 1e6 for k, v in phase_ns.items()},

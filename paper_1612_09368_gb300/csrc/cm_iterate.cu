@@ -334,7 +334,7 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
                     break;
                 }
                 __nanosleep(nap);
-                if (nap < 2048) nap <<= 1;
+                if (nap < 512) nap <<= 1;
             }
             idx++;
             left--;
