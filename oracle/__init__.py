@@ -81,6 +81,7 @@ def load(plant: int = 0):
             "or_delete_vertices": (i64, [vp, i32, _i32p, i32]),
             "or_batch_begin": (i64, [vp, i32, _i32p, i64]),
             "or_batch_step": (i32, [vp, _i32p, _i64p, _i32p, _i64p]),
+            "or_set_selection": (None, [vp, i32, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -128,7 +129,11 @@ class OracleError(RuntimeError):
 class OracleGraph:
     """Dynamic graph with core numbers maintained by O3 (mode 0) or O4 (mode 1)."""
 
-    def __init__(self, n: int, edges, cores=None, mode: int = SUPERIOR, plant: int = 0):
+    def __init__(self, n: int, edges, cores=None, mode: int = SUPERIOR, plant: int = 0,
+                 select_order: int = 0, select_rounds: int = 0):
+        """select_order / select_rounds: the variants of reading R1 for O4
+        (1 = canonical-key order instead of its fmix64; R > 0 = at most R
+        claim rounds per iteration)."""
         self._L = load(plant)
         e = _e(edges)
         c = None if cores is None else np.ascontiguousarray(cores, dtype=np.int32)
@@ -136,6 +141,7 @@ class OracleGraph:
         if not self._h:
             raise MemoryError("or_create")
         self.mode = mode
+        self._L.or_set_selection(self._h, int(select_order), int(select_rounds))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -35,7 +35,13 @@
  *     increasing priority, every remaining edge none of whose constrained
  *     endpoints (endpoints whose core equals the edge's core number,
  *     Section IV) is already taken.  The result satisfies Definition 6 (ii) at
- *     every level and is maximal.
+ *     every level and is maximal.  Two variants (or_set_selection): the
+ *     canonical key itself as the priority (lexicographic order), and the
+ *     selection run as claim rounds capped at R per iteration -- in a round
+ *     every eligible edge bids at its constrained endpoints and an edge
+ *     holding the least bid at all of them is selected; run to the end, the
+ *     rounds give the same set as the greedy pass, capped they give a
+ *     superior edge set that may not be maximal.
  *  R2 The level set C of Algorithm 1 is recomputed from the remaining edges
  *     at the start of every iteration, as Algorithm 5 does explicitly.
  *  R3 Algorithm 3's "if cd[r] >= 0 then cd[r] <- CSD else cd[r] += CSD" is
@@ -215,6 +221,7 @@ typedef struct {
     /* batch bookkeeping */
     uint32_t* taken; uint32_t stamp;
     int64_t nrem, remcap; int32_t* rem; uint64_t* remprio; int32_t bop;
+    int32_t sel_order, sel_rounds;    /* R1 variants: 1 = key order; R > 0 = claim rounds capped at R */
     int64_t iters, logcap, nlog; int64_t* log;
 } or_graph;
 
@@ -529,7 +536,8 @@ int64_t or_batch_begin(or_graph* g, int32_t op, const int32_t* e, int64_t k) {
     for (int64_t i = 0; i < c; i++) {
         int32_t u = keep[2 * i], v = keep[2 * i + 1];
         uint32_t lo = (uint32_t)(u < v ? u : v), hi = (uint32_t)(u < v ? v : u);
-        pr[i].prio = or_fmix64(((uint64_t)lo << 32) | hi); pr[i].idx = i;
+        const uint64_t key = ((uint64_t)lo << 32) | hi;
+        pr[i].prio = g->sel_order == 1 ? key : or_fmix64(key); pr[i].idx = i;
     }
     qsort(pr, (size_t)c, sizeof(pr_t), cmp_pr);        /* priorities are distinct (bijection) */
     free(g->rem); free(g->remprio);
@@ -544,6 +552,70 @@ int64_t or_batch_begin(or_graph* g, int32_t op, const int32_t* e, int64_t k) {
     return c;
 }
 
+/* Selection as claim rounds (reading R1, capped variant).  Round after
+ * round, every remaining edge that is not selected and none of whose
+ * constrained endpoints is taken bids its priority at its constrained
+ * endpoints; each edge whose bid is the least at every one of them is
+ * selected and takes them.  Stops when a round had no losing bid, or after
+ * g->sel_rounds rounds.  Writes the selected edges and their levels and
+ * keeps the rest, in priority order, as the remaining edges. */
+static void claim_rounds(or_graph* g, int32_t* sel, int32_t* lvl, int64_t* ns_out) {
+    const int64_t nrem = g->nrem;
+    uint64_t* best = (uint64_t*)malloc((size_t)(g->n + 1) * sizeof(uint64_t));
+    uint8_t* chosen = (uint8_t*)calloc((size_t)nrem + 1, 1);
+    uint8_t* bids = (uint8_t*)calloc((size_t)nrem + 1, 1);
+    for (int32_t round = 0; round < g->sel_rounds; round++) {
+        for (int64_t i = 0; i < nrem; i++) { best[g->rem[2 * i]] = UINT64_MAX; best[g->rem[2 * i + 1]] = UINT64_MAX; }
+        int64_t nbid = 0, nwin = 0;
+        for (int64_t i = 0; i < nrem; i++) {
+            int32_t u = g->rem[2 * i], v = g->rem[2 * i + 1];
+            int32_t k = g->core[u] < g->core[v] ? g->core[u] : g->core[v];
+            int cu = g->core[u] == k, cv = g->core[v] == k;
+            bids[i] = !chosen[i] && !(cu && g->taken[u] == g->stamp) && !(cv && g->taken[v] == g->stamp);
+            if (!bids[i]) continue;
+            nbid++;
+            if (cu && g->remprio[i] < best[u]) best[u] = g->remprio[i];
+            if (cv && g->remprio[i] < best[v]) best[v] = g->remprio[i];
+        }
+        for (int64_t i = 0; i < nrem; i++) {
+            if (!bids[i]) continue;
+            int32_t u = g->rem[2 * i], v = g->rem[2 * i + 1];
+            int32_t k = g->core[u] < g->core[v] ? g->core[u] : g->core[v];
+            int cu = g->core[u] == k, cv = g->core[v] == k;
+            if ((!cu || best[u] == g->remprio[i]) && (!cv || best[v] == g->remprio[i])) { chosen[i] = 1; nwin++; }
+        }
+        for (int64_t i = 0; i < nrem; i++) {       /* winners take their constrained endpoints */
+            if (!bids[i] || !chosen[i]) continue;
+            int32_t u = g->rem[2 * i], v = g->rem[2 * i + 1];
+            int32_t k = g->core[u] < g->core[v] ? g->core[u] : g->core[v];
+            if (g->core[u] == k) g->taken[u] = g->stamp;
+            if (g->core[v] == k) g->taken[v] = g->stamp;
+        }
+        if (nwin == nbid) break;                    /* no bid lost: the set is maximal */
+    }
+    int64_t ns = 0, nr = 0;
+    for (int64_t i = 0; i < nrem; i++) {
+        int32_t u = g->rem[2 * i], v = g->rem[2 * i + 1];
+        if (chosen[i]) {
+            int32_t k = g->core[u] < g->core[v] ? g->core[u] : g->core[v];
+            sel[2 * ns] = u; sel[2 * ns + 1] = v; lvl[ns] = k; ns++;
+        } else {
+            g->rem[2 * nr] = u; g->rem[2 * nr + 1] = v; g->remprio[nr] = g->remprio[i]; nr++;
+        }
+    }
+    g->nrem = nr;
+    *ns_out = ns;
+    free(best); free(chosen); free(bids);
+}
+
+/* Selection variants of reading R1: order 1 ranks edges by their canonical
+ * key instead of its fmix64; rounds > 0 caps the claim rounds per
+ * iteration.  Takes effect at the next batch. */
+void or_set_selection(or_graph* g, int32_t order, int32_t rounds) {
+    g->sel_order = order == 1 ? 1 : 0;
+    g->sel_rounds = rounds > 0 ? rounds : 0;
+}
+
 /* One iteration of Algorithm 1 (op 0) or Algorithm 5 (op 1).  Optionally
  * reports the selected edges and the changed vertices.  Returns 1 if an
  * iteration ran, 0 if no edges remained. */
@@ -556,22 +628,26 @@ int32_t or_batch_step(or_graph* g, int32_t* sel_out, int64_t* nsel_out, int32_t*
     int32_t* sel = (int32_t*)malloc((size_t)(2 * g->nrem + 2) * sizeof(int32_t));
     int32_t* lvl = (int32_t*)malloc((size_t)(g->nrem + 1) * sizeof(int32_t));
     int64_t ns = 0, nr = 0;
-    for (int64_t i = 0; i < g->nrem; i++) {
-        int32_t u = g->rem[2 * i], v = g->rem[2 * i + 1];
-        int32_t k = g->core[u] < g->core[v] ? g->core[u] : g->core[v];
-        int cu = g->core[u] == k, cv = g->core[v] == k;      /* constrained endpoints */
+    if (g->sel_rounds > 0) {
+        claim_rounds(g, sel, lvl, &ns);
+    } else {
+        for (int64_t i = 0; i < g->nrem; i++) {
+            int32_t u = g->rem[2 * i], v = g->rem[2 * i + 1];
+            int32_t k = g->core[u] < g->core[v] ? g->core[u] : g->core[v];
+            int cu = g->core[u] == k, cv = g->core[v] == k;      /* constrained endpoints */
 #if PLANT == 6
-        cv = 0;
+            cv = 0;
 #endif
-        if ((cu && g->taken[u] == g->stamp) || (cv && g->taken[v] == g->stamp)) {
-            g->rem[2 * nr] = u; g->rem[2 * nr + 1] = v; g->remprio[nr] = g->remprio[i]; nr++;
-            continue;
+            if ((cu && g->taken[u] == g->stamp) || (cv && g->taken[v] == g->stamp)) {
+                g->rem[2 * nr] = u; g->rem[2 * nr + 1] = v; g->remprio[nr] = g->remprio[i]; nr++;
+                continue;
+            }
+            if (cu) g->taken[u] = g->stamp;
+            if (cv) g->taken[v] = g->stamp;
+            sel[2 * ns] = u; sel[2 * ns + 1] = v; lvl[ns] = k; ns++;
         }
-        if (cu) g->taken[u] = g->stamp;
-        if (cv) g->taken[v] = g->stamp;
-        sel[2 * ns] = u; sel[2 * ns + 1] = v; lvl[ns] = k; ns++;
+        g->nrem = nr;
     }
-    g->nrem = nr;
     /* insert / delete the union of the E_k (Algorithm 1 lines 4-5, Algorithm 5 lines 4-5) */
     for (int64_t i = 0; i < ns; i++) {
         if (op == 0) add_edge(g, sel[2 * i], sel[2 * i + 1]);

@@ -201,9 +201,12 @@ def _constrained(core, u, v):
     return [x for x in (u, v) if core[x] == k], k
 
 
-def run_batch_with_invariants(og, op, batch, plant=0):
+def run_batch_with_invariants(og, op, batch, plant=0, maximal=True, log=None):
     """Runs one O4 batch through the stepper and asserts the per-iteration
-    invariants; returns the number of iterations."""
+    invariants; returns the number of iterations.  maximal=False for a
+    selection whose claim rounds are capped (the set is a superior edge set
+    but need not be maximal).  log: a list that receives each iteration's
+    selected edges."""
     cur = _canon(og.edges())
     seen, rem = set(), []
     for u, v in np.asarray(batch).reshape(-1, 2):
@@ -240,8 +243,11 @@ def run_batch_with_invariants(og, op, batch, plant=0):
             for x in cons:
                 assert x not in taken, "Definition 6 (ii): one edge per constrained endpoint"
                 taken[x] = (u, v)
+        assert selk, "every iteration selects an edge"
+        if log is not None:
+            log.append([tuple(int(x) for x in e) for e in sel])
         remset -= selk
-        for u, v in remset:
+        for u, v in (remset if maximal else ()):
             cons, _ = _constrained(before, u, v)
             assert any(x in taken for x in cons), "selection is maximal"
         after = og.cores()
@@ -255,7 +261,8 @@ def run_batch_with_invariants(og, op, batch, plant=0):
         for x in moved:
             assert before[x] in levels, "Lemmas 1-2 (ii): only vertices at a selected level change"
     assert not remset
-    assert iters <= max(2 * delta_b - 1, 0), (iters, delta_b)
+    if maximal:
+        assert iters <= max(2 * delta_b - 1, 0), (iters, delta_b)
     return iters
 
 
@@ -280,6 +287,76 @@ def check_o4_batches(plant=0, trials=10, seed=7):
                 batch = np.array([lst[i] for i in idx] + [(0, n - 1)], dtype=np.int32).reshape(-1, 2)
                 run_batch_with_invariants(og, oracle.DELETE, batch, plant)
             assert (og.cores() == oracle.bz(n, og.edges(), plant)).all(), (t, b)
+
+
+def check_selection_order_worked_examples(plant=0):
+    """Worked examples of the selection variants, derived by hand.
+    (1) K5 on 0..4 (core 4) and an isolated vertex 5: inserting 5-0 .. 5-4
+    (giving K6, core 5) constrains vertex 5 in every edge, so each
+    iteration selects one edge, in
+    increasing priority: by key (0,5), (1,5), ..., (4,5); by fmix64 of the
+    key in that order.  (2) Four isolated vertices and the inserted path
+    0-1, 1-2, 2-3 in key order: the claim rounds select (0,1) in round one
+    and (2,3) in round two, then (1,2) in the next iteration -- two
+    iterations; capped at one round per iteration, three: (0,1), then (1,2)
+    (vertex 2 is its only constrained endpoint once 1 has core 1), then
+    (2,3)."""
+    k5 = [(a, b) for a in range(5) for b in range(a + 1, 5)]
+    batch = np.array([(5, 3), (5, 0), (5, 4), (5, 1), (5, 2)], dtype=np.int32)
+    for order in (0, 1):
+        for rounds in (0, 1):
+            og = oracle.OracleGraph(6, k5, mode=oracle.SUPERIOR, plant=plant, select_order=order,
+                                    select_rounds=rounds)
+            got = []
+            run_batch_with_invariants(og, oracle.INSERT, batch, plant, maximal=rounds == 0, log=got)
+            keys = [(x, 5) for x in range(5)]
+            if order == 0:
+                keys.sort(key=lambda e: oracle.fmix64((e[0] << 32) | e[1], plant))
+            assert [sorted(map(tuple, map(sorted, it))) for it in got] == [[k] for k in keys], (order, rounds, got)
+            assert (og.cores() == 5).all()   # K6
+    path = np.array([(2, 3), (0, 1), (1, 2)], dtype=np.int32)
+    for rounds, want in ((0, [[(0, 1), (2, 3)], [(1, 2)]]), (1, [[(0, 1)], [(1, 2)], [(2, 3)]]),
+                         (2, [[(0, 1), (2, 3)], [(1, 2)]])):
+        og = oracle.OracleGraph(4, np.zeros((0, 2), np.int32), mode=oracle.SUPERIOR, plant=plant, select_order=1,
+                                select_rounds=rounds)
+        got = []
+        run_batch_with_invariants(og, oracle.INSERT, path, plant, maximal=rounds != 1, log=got)
+        assert [sorted(tuple(sorted(e)) for e in it) for it in got] == want, (rounds, got)
+        assert (og.cores() == np.array([1, 1, 1, 1])).all()
+
+
+def check_selection_variants(plant=0, trials=6, seed=11):
+    """Every selection variant reaches the cores of O1 after every batch, and
+    claim rounds run to the end select, iteration by iteration, exactly the
+    greedy pass's sets (the least-priority-first maximal set)."""
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        n = int(rng.integers(12, 70))
+        e = _rand_graph(rng, n, rng.uniform(0.05, 0.25))
+        for order in (0, 1):
+            gs = {r: oracle.OracleGraph(n, e, mode=oracle.SUPERIOR, plant=plant, select_order=order,
+                                        select_rounds=r) for r in (0, 1, 2, 1 << 20)}
+            for b in range(4):
+                cur = _canon(gs[0].edges())
+                if b % 2 == 0:
+                    batch = rng.integers(0, n, (int(rng.integers(1, 3 * n)), 2)).astype(np.int32)
+                    op = oracle.INSERT
+                else:
+                    lst = sorted(cur)
+                    idx = rng.permutation(len(lst))[: int(rng.integers(0, len(lst) + 1))]
+                    batch = np.array([lst[i] for i in idx] + [(0, n - 1)], dtype=np.int32).reshape(-1, 2)
+                    op = oracle.DELETE
+                logs, its = {}, {}
+                for r, og in gs.items():
+                    logs[r] = []
+                    its[r] = run_batch_with_invariants(og, op, batch, plant, maximal=r in (0, 1 << 20), log=logs[r])
+                canon = {r: [sorted(tuple(sorted(x)) for x in it) for it in lg] for r, lg in logs.items()}
+                assert canon[1 << 20] == canon[0], (t, order, b)
+                # (a capped selection need not take more iterations: a maximal
+                # set is not always the best next step)
+                ref = oracle.bz(n, gs[0].edges(), plant)
+                for r, og in gs.items():
+                    assert (og.cores() == ref).all(), (t, order, b, r)
 
 
 def check_vertex_ops(plant=0, seed=9):
@@ -327,4 +404,4 @@ def check_fmix64(plant=0):
 
 ALL = [check_brute_closed_forms, check_bz_closed_forms, check_bz_vs_brute_exhaustive,
        check_bz_vs_brute_random, check_golden, check_o3_every_edge, check_o4_batches,
-       check_vertex_ops, check_fmix64]
+       check_selection_order_worked_examples, check_selection_variants, check_vertex_ops, check_fmix64]
