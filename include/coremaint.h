@@ -85,8 +85,19 @@ typedef struct cm_options {
                                is scanned by a whole block instead of one warp (4096) */
     int32_t block_slots_delete; /* the same for delete calls (1024) */
     int32_t task_claim;     /* grid mode: most search tasks a warp claims at once (1..8, default 1) */
-    int32_t reserved;
+    int32_t select_order;   /* order of the greedy superior-edge-set selection (Section IV,
+                               Definition 6 and Algorithm 2): CM_SELECT_HASH (default) ranks an edge
+                               by fmix64 of its canonical key (lo << 32 | hi), a fixed pseudo-random
+                               order; CM_SELECT_KEY by the canonical key itself (lexicographic) */
+    int32_t select_rounds;  /* claim rounds per iteration: 0 (default) = until the selected set is
+                               maximal; R > 0 = at most R rounds (still a superior edge set, perhaps
+                               not a maximal one: fewer barriers per iteration, perhaps more
+                               iterations).  Final cores do not depend on either choice. */
+    int32_t reserved[3];
 } cm_options;
+
+#define CM_SELECT_HASH 0
+#define CM_SELECT_KEY 1
 
 /* Test hook: every grid barrier of the next maintenance launch waits for
  * one more block than exists, so each wait runs out after spin_limit_ns and

@@ -40,6 +40,8 @@ CM_ERR_STATE = -6
 CM_OP_INSERT = 0
 CM_OP_DELETE = 1
 CM_DEBUG_BARRIER_NEVER_RELEASES = 1
+CM_SELECT_HASH = 0
+CM_SELECT_KEY = 1
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -52,7 +54,8 @@ class cm_options(ctypes.Structure):
         ("spin_limit_ns", ctypes.c_int64), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("debug_flags", ctypes.c_int32), ("block_mode_enter", ctypes.c_int32), ("block_mode_leave", ctypes.c_int32),
         ("hub_slots", ctypes.c_int32), ("block_slots", ctypes.c_int32), ("block_slots_delete", ctypes.c_int32),
-        ("task_claim", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("task_claim", ctypes.c_int32), ("select_order", ctypes.c_int32), ("select_rounds", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

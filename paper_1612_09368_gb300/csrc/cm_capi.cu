@@ -72,6 +72,7 @@ struct cm_graph {
     int32_t hub_len = 1024;
     int32_t block_len = 4096, block_len_del = 1024;
     int32_t claim_max = 1;
+    int32_t sel_key = 0, sel_rounds = 0;   // selection order and claim-round cap (options)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -474,6 +475,8 @@ static int create_common(int32_t n, const int32_t* edges, long long m, const int
     h->block_len = h->opt.block_slots >= 32 ? h->opt.block_slots : 4096;
     h->block_len_del = h->opt.block_slots_delete >= 32 ? h->opt.block_slots_delete : 1024;
     h->claim_max = h->opt.task_claim >= 1 && h->opt.task_claim <= 8 ? h->opt.task_claim : 1;
+    h->sel_key = h->opt.select_order == CM_SELECT_KEY ? 1 : 0;
+    h->sel_rounds = h->opt.select_rounds > 0 ? h->opt.select_rounds : 0;
     CK(h, cudaGetDevice(&h->device));
     CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     int coop = 0;
@@ -694,6 +697,8 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         p.hub_len = h->hub_len;
         p.block_len = op == CM_OP_INSERT ? h->block_len : h->block_len_del;
         p.claim_max = h->claim_max;
+        p.sel_key = h->sel_key;
+        p.sel_rounds = h->sel_rounds;
         int blocks, threads;
         persistent_geometry(h, 0, nrem0, &blocks, &threads);
         p.expect = (uint32_t)blocks;
@@ -1254,6 +1259,8 @@ static MaintainParams step_params(const cm_step* s, int op, int* blocks, int* th
     p.hub_len = c.hub_slots > 0 ? (c.hub_slots < 128 ? 128 : c.hub_slots) : c.hub_slots < 0 ? 0 : 1024;
     p.block_len = op == CM_OP_INSERT ? (c.block_slots >= 32 ? c.block_slots : 4096) : h->block_len_del;
     p.claim_max = c.task_claim >= 1 && c.task_claim <= 8 ? c.task_claim : 1;
+    p.sel_key = h->sel_key;
+    p.sel_rounds = h->sel_rounds;
     int occ = maintain_blocks_per_sm(kGridThreadsHost);
     if (occ < 1) occ = 1;
     int bps = c.blocks_per_sm > 0 && c.blocks_per_sm < occ ? c.blocks_per_sm : occ;

@@ -402,8 +402,15 @@ __device__ __forceinline__ void edge_level(const DevGraph& g, const REdge& E, in
     chi = b.x == k && b.y < PIN_SD;
 }
 
+// An edge's selection priority (smaller wins): fmix64 of its canonical key,
+// a bijection, or the key itself (lexicographic order of (lo, hi)).
+__device__ __forceinline__ unsigned long long edge_prio(const REdge& E, bool by_key) {
+    const unsigned long long key = ekey(E.lo, E.hi);
+    return by_key ? key : fmix64(key);
+}
+
 // Selection, claim phase of round r.
-__device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e) {
+__device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e, bool by_key) {
     REdge E = R[i];
     int k; bool clo, chi;
     edge_level(g, E, k, clo, chi);
@@ -418,7 +425,7 @@ __device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long lon
         R[i].flags = f | F_BLK;
         return;
     }
-    unsigned long long prio = fmix64(ekey(E.lo, E.hi));
+    const unsigned long long prio = edge_prio(E, by_key);
     unsigned long long* cb = (r & 1) ? g.claim1 : g.claim0;
     if (clo) atomicMin(&cb[E.lo], prio);
     if (chi) atomicMin(&cb[E.hi], prio);
@@ -427,12 +434,12 @@ __device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long lon
 
 // Selection, check phase of round r.  Returns 1 if the edge claimed and lost.
 __device__ __forceinline__ int check_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e,
-                                          long long& nsel) {
+                                          long long& nsel, bool by_key) {
     REdge E = R[i];
     if ((E.flags >> 2) != (uint32_t)(r + 1)) return 0;
     int k; bool clo, chi;
     edge_level(g, E, k, clo, chi);
-    unsigned long long prio = fmix64(ekey(E.lo, E.hi));
+    const unsigned long long prio = edge_prio(E, by_key);
     const unsigned long long* cb = (r & 1) ? g.claim1 : g.claim0;
     bool win = (!clo || cb[E.lo] == prio) && (!chi || cb[E.hi] == prio);
     if (!win) return 1;
@@ -547,19 +554,20 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             if (MODE == 0 && r == 0) reset_tasks();   // nobody pushes tasks before APPLY
             for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
                 long long i = base + lane;
-                if (i < (long long)nrem) claim_edge(g, Rc, i, r, e);
+                if (i < (long long)nrem) claim_edge(g, Rc, i, r, e, P.sel_key != 0);
             }
             if (!(ok = sync(PH_CLAIM))) break;
             int lost = 0;
             for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
                 long long i = base + lane;
-                if (i < (long long)nrem) lost += check_edge(g, Rc, i, r, e, ls.sel);
+                if (i < (long long)nrem) lost += check_edge(g, Rc, i, r, e, ls.sel, P.sel_key != 0);
             }
             lost = warp_sum(lost);
             if (lane == 0 && lost) atomicAdd(&C->pc[0], (unsigned long long)lost);
             if (!(ok = sync(PH_CHECK))) break;
             r++;
-            if (vload64(&C->spc[0]) == 0) break;
+            if (vload64(&C->spc[0]) == 0) break;           // no edge lost: the set is maximal
+            if (P.sel_rounds > 0 && r >= P.sel_rounds) break;   // capped: a superior edge set all the same
         }
         if (!ok) break;
         rounds += r;

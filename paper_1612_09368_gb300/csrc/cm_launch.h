@@ -40,6 +40,8 @@ struct MaintainParams {
     int32_t hub_len;          // grid mode: vertices with at least this many slots are scanned grid-wide
     int32_t block_len;        // vertices with at least this many slots are scanned by a whole block
     int32_t claim_max;        // grid-mode task queue: most slots a warp claims at once
+    int32_t sel_key;          // selection order: 0 fmix64 of the canonical key, 1 the key itself
+    int32_t sel_rounds;       // claim rounds per iteration (0 = until the set is maximal)
     int32_t use_cond;         // inside a captured step: the single-block kernel drives the loop node
     unsigned long long cond;  // that node's conditional handle
 };

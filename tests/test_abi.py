@@ -31,8 +31,8 @@ def test_library_exports_every_declared_entry_point(so):
 
 def test_binding_struct_layouts_match_header():
     import paper_1612_09368_gb300 as cm
-    # cm_options: 6 int32, int64, 3 pointers, 8 int32
-    assert ctypes.sizeof(cm.cm_options) == 6 * 4 + 8 + 3 * 8 + 8 * 4
+    # cm_options: 6 int32, int64, 3 pointers, 12 int32
+    assert ctypes.sizeof(cm.cm_options) == 6 * 4 + 8 + 3 * 8 + 12 * 4
     assert ctypes.sizeof(cm.cm_step_config) == 8 * 4
     # cm_stats: 14 int64, 2 double, peel_levels, barriers, grid_iterations, phase_ns[7], reserved[4]
     assert ctypes.sizeof(cm.cm_stats) == 14 * 8 + 2 * 8 + (3 + 7 + 4) * 8
@@ -44,6 +44,7 @@ def test_default_options_without_gpu(so):
     assert (o.slack_pct, o.min_cap, o.block_threads, o.spin_limit_ns) == (25, 4, 512, 4_000_000_000)
     assert (o.block_mode_edges, o.block_mode_enter, o.block_mode_leave) == (16384, 1024, 8192)
     assert (o.hub_slots, o.block_slots, o.block_slots_delete, o.task_claim) == (1024, 4096, 1024, 1)
+    assert (o.select_order, o.select_rounds) == (cm.CM_SELECT_HASH, 0)
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):

@@ -109,6 +109,43 @@ def test_random_batches_small(cm, seed):
         assert g.m == ref.m
 
 
+@pytest.mark.parametrize("order,rounds", [(1, 0), (0, 1), (0, 2), (1, 1)])
+def test_selection_variants(cm, order, rounds):
+    """The selection variants of reading R1 (Section IV, Definition 6 and
+    Algorithm 2): canonical-key order instead of its fmix64, and claim
+    rounds capped per iteration.  The cores equal the oracle's after every
+    batch and the iteration counts equal O4's under the same variant, on
+    small graphs and on a 20,000-vertex BA graph (one core level)."""
+    rng = np.random.default_rng(200 + 10 * order + rounds)
+    opts = dict(select_order=order, select_rounds=rounds)
+    for trial in range(3):
+        n = int(rng.integers(50, 400))
+        e = _rand_graph(rng, n, rng.uniform(0.02, 0.15))
+        g = cm.CoreGraph(n, _dev(e), **opts)
+        ref = oracle.OracleGraph(n, e, mode=oracle.SUPERIOR, **opts)
+        for b in range(6):
+            cur = ref.edges()
+            if b % 2 == 0 or len(cur) == 0:
+                batch = rng.integers(0, n, (int(rng.integers(1, 4 * n)), 2)).astype(np.int32)
+                got, exp = g.insert_edges(_dev(batch)), ref.insert_edges(batch)
+            else:
+                batch = cur[rng.permutation(len(cur))[: int(rng.integers(1, len(cur) + 1))]]
+                got, exp = g.delete_edges(_dev(batch)), ref.delete_edges(batch)
+            assert got == exp
+            assert g.stats()["iterations"] == ref.last_iterations(), (trial, b)
+            _check_same(g, ref, f"variant {order}/{rounds} trial {trial} batch {b}")
+    n = 20000
+    e = synth.ba(n, 6, synth.stream(21))
+    dyn = synth.DynGraph(n, e)
+    g = cm.CoreGraph(n, _dev(e), **opts)
+    ref = oracle.OracleGraph(n, e, mode=oracle.SUPERIOR, **opts)
+    ins = dyn.sample_insert(3000, synth.PREFERENTIAL, synth.stream(21, 0, 0, synth.INSERT))
+    g.insert_edges(_dev(ins))
+    ref.insert_edges(ins)
+    assert g.stats()["iterations"] == ref.last_iterations()
+    _check_same(g, ref, "BA insert")
+
+
 def test_cfg_er_insert_then_delete_full_size(cm):
     """ER G(n=10,000, m=50,000), 1,000 new edges inserted, then 1,000 existing
     edges deleted; cores checked after each batch (the small workload)."""
