@@ -279,7 +279,9 @@ def run_sweep(args):
         r1.record(stream)
         r1.synchronize()
         rp = r0.elapsed_time(r1)
-        levels = g.stats()["peel_levels"]
+        pst = g.stats()
+        levels = pst["peel_levels"]
+        peel_gbs = pst["alg_bytes"] / (pst["maintain_ms"] / 1000.0) / 1e9 if pst["maintain_ms"] else 0.0
         g.apply_edges(cm.CM_OP_DELETE if op == "insert" else cm.CM_OP_INSERT, db)
         g.recompute_cores()
         call_ms = statistics.median(ms)
@@ -290,7 +292,8 @@ def run_sweep(args):
                     "maintain_ms": st["maintain_ms"], "alg_bytes": st["alg_bytes"], "achieved_gbs": achieved,
                     "frac": achieved / peak, "visited": st["visited"], "visited_slots": st["visited_slots"],
                     "evicted": st["evicted"], "evicted_slots": st["evicted_slots"], "changed": st["changed"],
-                    "repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": levels})
+                    "repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": levels,
+                    "peel_gbs": peel_gbs, "peel_frac": peel_gbs / peak, "peel_subwaves": pst["waves"]})
         cases.append(rec)
         print(json.dumps(rec), file=sys.stderr, flush=True)
     clocks = clk.stop()
@@ -866,8 +869,13 @@ def main():
         r1.synchronize()
         rp_ms = r0.elapsed_time(r1)
         mi = statistics.median(per_call_ms["insert"])
+        pst = g.stats()
+        pk, _ = load_peaks()
+        pgbs = pst["alg_bytes"] / (pst["maintain_ms"] / 1000.0) / 1e9 if pst["maintain_ms"] else 0.0
         repeel = {"repeel_ms": rp_ms, "maintain_insert_1e4_ms_median": mi, "speedup": rp_ms / mi,
-                  "peel_levels": g.stats()["peel_levels"]}
+                  "peel_levels": pst["peel_levels"], "peel_subwaves": pst["waves"],
+                  "peel_roofline": {"peel_and_sd_ms": pst["maintain_ms"], "alg_bytes": pst["alg_bytes"],
+                                    "achieved_gbs": pgbs, "frac": pgbs / pk if pk else None}}
 
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (maint_ms / 1000.0) / 1e9 if maint_ms > 0 else 0.0

@@ -118,7 +118,8 @@ typedef struct cm_stats {
     int64_t changed;         /* vertices whose core moved by one */
     int64_t changed_slots;
     int64_t waves;           /* discovery + eviction waves */
-    int64_t alg_bytes;       /* algorithmic HBM bytes of the maintenance kernel (see design notes) */
+    int64_t alg_bytes;       /* algorithmic HBM bytes of the maintenance kernel; for cm_recompute_cores,
+                                of the peel and the SD pass (see design notes) */
     int64_t launches;        /* kernels this library launched during the call */
     double maintain_ms;      /* device time of the maintenance kernel (CUDA events on the handle's stream) */
     double call_ms;          /* device time of the whole call, first copy to last kernel */

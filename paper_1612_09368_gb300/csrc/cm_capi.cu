@@ -574,6 +574,14 @@ static int peel_all(cm_graph* h) {
         return set_err(h, CM_ERR_LIMIT, "peeling stopped with device error %d", h->hctl->error);
     }
     h->last.peel_levels = (int64_t)h->hctl->st[ST_LEVELS];
+    h->last.waves = (int64_t)h->hctl->st[ST_WAVES];   // sub-waves of the peel
+    // Algorithmic bytes of the peel: 16 B per vertex to start it (degree
+    // read, working degree, core and list writes); 16 B per remaining-list
+    // entry scanned at a level (id, core, working degree, list write); 12 B
+    // per adjacency slot of a peeled vertex (neighbour id, its core, the
+    // working-degree atomic).
+    h->last.alg_bytes += 16 * (int64_t)h->n + 16 * (int64_t)h->hctl->st[ST_VISITED] +
+                         12 * (int64_t)h->hctl->st[ST_VISSLOTS];
     return CM_OK;
 }
 
@@ -611,6 +619,9 @@ extern "C" int cm_recompute_cores(cm_graph* h) {
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
     h->last.maintain_ms = ms;
+    // the superior degrees after the peel: 16 B per vertex (offset, length,
+    // SD write) and 8 B per adjacency entry (neighbour id and core)
+    h->last.alg_bytes += 16 * (int64_t)h->n + 16 * (int64_t)h->m;
     h->cores_stale = false;
     return end_call(h, CM_OK);
 }

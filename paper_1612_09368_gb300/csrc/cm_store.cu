@@ -179,8 +179,10 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
     int k = 0;
     unsigned long long ft = 0;
     long long levels = 0;
+    long long slots = 0;   // adjacency slots this warp scanned (algorithmic-byte counters)
     while (nl > 0) {
         // scan the remaining list
+        if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_VISITED] += nl;
         const unsigned long long f0 = ft;
         int mx = 0;   // max of (INT_MAX - degree) over survivors: gives the min degree
         for (long long base = gwarp * 32; base < (long long)nl; base += nwarps * 32) {
@@ -218,32 +220,50 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
             k = 0x7FFFFFFF - (int)smx;   // jump to the smallest remaining degree
             continue;
         }
-        // sub-waves at level k
+        // sub-waves at level k.  A peeled neighbour needs no test: its
+        // working degree is at most k when it leaves and only falls after,
+        // so a decrement can bring exactly k + 1 down to k only for a
+        // vertex still in the graph.
         unsigned long long lo = f0, hi = fhi;
         while (hi > lo) {
             const unsigned long long cnt = hi - lo;
+            // a warp takes a run of frontier vertices per claim: up to 32
+            // when the wave is wide (fewer claims on the shared counter),
+            // one when it is narrow (no warp left idle)
+            const unsigned long long run = min(32ull, max(1ull, cnt / ((unsigned long long)nwarps * 4ull)));
             for (;;) {
-                unsigned long long j = 0;
-                if (lane == 0) j = atomicAdd(&C->pc[2], 1ull);
-                j = __shfl_sync(0xffffffffu, j, 0);
-                if (j >= cnt) break;
-                int v = P.F[lo + j];
-                long long o = g.off[v];
-                int len = g.end[v];
-                for (int t0 = 0; t0 < len; t0 += 32) {
-                    int tt = t0 + lane;
-                    int w = tt < len ? g.adj[o + tt] : HOLE;
-                    bool p = false;
-                    if (w >= 0 && g.hs[w].x == UNPEELED) {
-                        if (atomicSub(&P.dcur[w], 1) == k + 1) {
-                            g.hs[w].x = k;
-                            p = true;
+                unsigned long long j0 = 0;
+                if (lane == 0) j0 = atomicAdd(&C->pc[2], run);
+                j0 = __shfl_sync(0xffffffffu, j0, 0);
+                if (j0 >= cnt) break;
+                const unsigned long long j1 = min(cnt, j0 + run);
+                for (unsigned long long j = j0; j < j1; j++) {
+                    const int v = P.F[lo + j];
+                    const long long o = g.off[v];
+                    const int len = g.end[v];
+                    slots += len;
+                    // four slots per lane per step, one 16-byte load (lists
+                    // start 16-byte aligned, capacities are multiples of 4)
+                    for (int base = 0; base < len; base += 128) {
+                        const int t0 = base + lane * 4;
+                        int4 a = make_int4(HOLE, HOLE, HOLE, HOLE);
+                        if (t0 < len) a = __ldcs(reinterpret_cast<const int4*>(g.adj + o + t0));
+                        const int w[4] = {a.x, t0 + 1 < len ? a.y : HOLE, t0 + 2 < len ? a.z : HOLE,
+                                          t0 + 3 < len ? a.w : HOLE};
+                        int r[4];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) r[q] = w[q] >= 0 ? atomicSub(&P.dcur[w[q]], 1) : 0;
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const bool p = w[q] >= 0 && r[q] == k + 1;
+                            if (p) g.hs[w[q]].x = k;
+                            warp_push(&C->tail[0], P.F, ~0ull, p, w[q]);
                         }
                     }
-                    warp_push(&C->tail[0], P.F, ~0ull, p, w);
                 }
             }
             if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+            if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
             lo = hi;
             hi = vload64(&C->stail[0]);
         }
@@ -252,6 +272,7 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
         levels++;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_LEVELS] = (unsigned long long)levels;
+    if (lane == 0 && slots) atomicAdd(&C->st[ST_VISSLOTS], (unsigned long long)slots);
 }
 
 int peel_blocks_per_sm(int threads) {
