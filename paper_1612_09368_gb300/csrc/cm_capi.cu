@@ -564,6 +564,9 @@ static int peel_all(cm_graph* h) {
     p.F = h->OVL;
     p.qmask = h->qmask;
     p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
+    // the frontier ring starts all -1: the peel's cascades wait on an entry
+    // until its producer has written a vertex id there
+    CK(h, cudaMemsetAsync(h->OVL, 0xFF, (size_t)(h->qmask + 1) * sizeof(int32_t), h->stream));
     int blocks, threads;
     persistent_geometry(h, 1, h->n, &blocks, &threads);
     p.expect = (uint32_t)blocks;
