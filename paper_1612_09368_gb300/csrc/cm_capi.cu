@@ -577,7 +577,7 @@ static int peel_all(cm_graph* h) {
         return set_err(h, CM_ERR_LIMIT, "peeling stopped with device error %d", h->hctl->error);
     }
     h->last.peel_levels = (int64_t)h->hctl->st[ST_LEVELS];
-    h->last.waves = (int64_t)h->hctl->st[ST_WAVES];   // sub-waves of the peel
+    h->last.waves = (int64_t)h->hctl->st[ST_WAVES];   // levels whose cascade ran
     // Algorithmic bytes of the peel: 16 B per vertex to start it (degree
     // read, working degree, core and list writes); 16 B per remaining-list
     // entry scanned at a level (id, core, working degree, list write); 12 B
