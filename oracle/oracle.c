@@ -648,7 +648,7 @@ int32_t or_batch_step(or_graph* g, int32_t* sel_out, int64_t* nsel_out, int32_t*
         }
         g->nrem = nr;
     }
-    /* insert / delete the union of the E_k (Algorithm 1 lines 4-5, Algorithm 5 lines 4-5) */
+    /* insert / delete the union of the E_k (Algorithms 1 and 5) */
     for (int64_t i = 0; i < ns; i++) {
         if (op == 0) add_edge(g, sel[2 * i], sel[2 * i + 1]);
         else del_edge(g, sel[2 * i], sel[2 * i + 1]);
@@ -667,7 +667,7 @@ int32_t or_batch_step(or_graph* g, int32_t* sel_out, int64_t* nsel_out, int32_t*
         nc += op == 0 ? k_superior_insert(g, ek, ne, k, chg + nc) : k_superior_delete(g, ek, ne, k, chg + nc);
         reset_scratch(g);
     }
-    /* Algorithm 1 line 7 / Algorithm 5 line 7 */
+    /* the last step of Algorithms 1 and 5: every vertex found moves by one */
     for (int64_t j = 0; j < nc; j++) g->core[chg[j]] += op == 0 ? 1 : -1;
     if (g->nlog == g->logcap) {
         g->logcap = g->logcap ? 2 * g->logcap : 64;

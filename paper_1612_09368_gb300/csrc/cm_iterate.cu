@@ -23,7 +23,10 @@
 //   APPLY    insert / delete the selected edges in the slack CSR and move
 //            SD (superior degree, Definition 7) of constrained endpoints.
 //   insert:  positive and negative search of Algorithms 3-4, run as
-//            breadth-first waves in which both progress together.  The
+//            breadth-first waves in which both progress together (single-
+//            block mode) or as a task queue without level barriers (grid
+//            mode, below async_search: the order of processing does not
+//            change the result).  The
 //            constrained endpoints are the first frontier.  Processing a
 //            frontier vertex v adds CSD(v) (Definition 8) to its support
 //            count, which already holds one decrement per evicted neighbour
@@ -35,12 +38,13 @@
 //            evicted too (InsertRemove, Algorithm 4).  Frontier and evictions
 //            of a wave run in the same phase, so evictions prune the search
 //            as it grows.  COMMIT: processed vertices still above k rise by
-//            one (Algorithm 1 line 7, Lemma 7).
-//   delete:  EVICT in waves from the constrained endpoints whose SD fell
-//            below k (Algorithm 6); an evicted vertex drops by one and takes
+//            one (the last step of Algorithm 1, Lemma 7).
+//   delete:  EVICT in waves (or, grid-wide, as queued tasks) from the
+//            constrained endpoints whose SD fell below k (Algorithm 6); an
+//            evicted vertex drops by one and takes
 //            one from the support (initially SD) of every core-k neighbour,
 //            which leaves when its support falls below k (DeleteRemove,
-//            Algorithm 7; Algorithm 5 line 7).
+//            Algorithm 7; the last step of Algorithm 5).
 //   FIX-UP   recompute SD of moved vertices and adjust SD of unmoved
 //            neighbours whose core equals the moved vertex's new core
 //            (insert) or old core (delete).  It only writes SD, which the
