@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -52,13 +53,22 @@ def load_peaks():
 KERNEL_SOURCES = ("cm_iterate.cu", "cm_vertex.cuh", "cm_common.cuh", "cm_launch.h")
 
 
+def _code_only(src: str) -> str:
+    """C++ source without comments and blank lines (a comment edit does not
+    change the compiled kernel)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_source_sha() -> str:
-    """Hash of the maintenance kernel's sources (the kernel file and the
-    headers it includes), to tell whether a stored ncu capture is current."""
+    """Hash of the maintenance kernel's code (the kernel file and the headers
+    it includes, comments removed), to tell whether a stored ncu capture is
+    current."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1612_09368_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1612_09368_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
