@@ -486,3 +486,17 @@ def test_torch_allocator_and_device_outputs(cm):
     assert (out.cpu().numpy() == oracle.bz(n, e)).all()
     g2 = cm.CoreGraph(n, e, use_torch_allocator=False)
     assert (g2.cores() == oracle.bz(n, e)).all()
+
+
+def test_readme_quick_start(cm):
+    """The README's example: a triangle with a pendant becomes K4 after two
+    inserts (cores 3), then deleting vertex 3 leaves the triangle (cores 2)
+    and a dead vertex (-1)."""
+    import torch
+    edges = torch.tensor([[0, 1], [1, 2], [2, 0], [2, 3]], dtype=torch.int32).cuda()
+    G = cm.CoreGraph(4, edges)
+    assert G.cores().tolist() == [2, 2, 2, 1]
+    assert G.insert_edges(torch.tensor([[3, 0], [3, 1]], dtype=torch.int32).cuda()) == 2
+    assert G.cores().tolist() == [3, 3, 3, 3]
+    G.delete_vertices(torch.tensor([3], dtype=torch.int32).cuda())
+    assert G.cores().tolist() == [2, 2, 2, -1]

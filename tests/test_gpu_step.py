@@ -99,6 +99,34 @@ def test_step_matches_oracle_over_replays(cm, stream):
     assert 1 <= cnt["captures"] <= 5
 
 
+def test_step_with_selection_variant(cm, stream):
+    """A captured step on a handle created with a selection variant
+    (canonical-key order, one claim round per iteration) matches the
+    oracle's superior-edge-set procedure under the same variant, iteration
+    count included."""
+    rng, ns, ms, parts = _many(3, 8)
+    ng = len(ns)
+    opts = dict(select_order=cm.CM_SELECT_KEY, select_rounds=1)
+    g = cm.CoreGraph(None, _dev(np.concatenate(parts)), multi=(ns, ms), stream=stream, **opts)
+    bases = g.bases()
+    union = oracle.OracleGraph(int(sum(ns)), np.concatenate([p + b for p, b in zip(parts, bases)]),
+                               mode=oracle.SUPERIOR, **opts)
+    dyns = [synth.DynGraph(ns[i], parts[i]) for i in range(ng)]
+    st = g.step(20000, 20000)
+    for step in range(3):
+        ins, dele = _batches(rng, dyns, 70, step)
+        ci, cd = [len(a) for a in ins], [len(x) for x in dele]
+        gi = np.concatenate([a + bases[i] for i, a in enumerate(ins)])
+        gd = np.concatenate([x + bases[i] for i, x in enumerate(dele)])
+        st.run(ci, _dev(np.concatenate(ins)), cd, _dev(np.concatenate(dele)))
+        union.insert_edges(gi)
+        it_ins = union.last_iterations()
+        union.delete_edges(gd)
+        it_del = union.last_iterations()
+        assert g.stats()["iterations"] == it_ins + it_del, step
+        assert (g.cores() == union.cores()).all(), step
+
+
 def test_step_single_graph_and_errors(cm, stream):
     n = 4000
     e = synth.er(n, 16000, synth.stream(80))
