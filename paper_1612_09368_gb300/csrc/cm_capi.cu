@@ -630,6 +630,64 @@ extern "C" int cm_recompute_cores(cm_graph* h) {
 }
 
 // ------------------------------------------------------------------ updates
+// Adds one maintenance call's device counters (Ctl::st / ph layout) to s.
+// Algorithmic bytes: per iteration 16 B per remaining edge (pair + both
+// cores) and 16 B per selected edge (claims, CSR writes); 16 B per visited
+// vertex (its row) plus 12 B per slot (neighbour id, core, SD); 12 B per
+// slot of an evicted vertex (id, core, support update); 8 B per changed
+// vertex plus 8 B per slot (id, core) for the SD fix-up.
+static void add_maintain_counters(cm_stats& s, const unsigned long long* st, const unsigned long long* ph) {
+    s.iterations += (int64_t)st[ST_ITERS];
+    s.select_rounds += (int64_t)st[ST_ROUNDS];
+    s.selected += (int64_t)st[ST_SELECTED];
+    s.remaining_sum += (int64_t)st[ST_REMSUM];
+    s.visited += (int64_t)st[ST_VISITED];
+    s.visited_slots += (int64_t)st[ST_VISSLOTS];
+    s.evicted += (int64_t)st[ST_EVICTED];
+    s.evicted_slots += (int64_t)st[ST_EVSLOTS];
+    s.changed += (int64_t)st[ST_CHANGED];
+    s.changed_slots += (int64_t)st[ST_CHSLOTS];
+    s.waves += (int64_t)st[ST_WAVES];
+    s.barriers += (int64_t)st[ST_BARRIERS];
+    s.grid_iterations += (int64_t)st[ST_GRID_ITERS];
+    for (int i = 0; i < PH_COUNT && i < 7; i++) s.phase_ns[i] += (int64_t)ph[i];
+    s.alg_bytes += 16 * (int64_t)st[ST_REMSUM] + 16 * (int64_t)st[ST_SELECTED] + 16 * (int64_t)st[ST_VISITED] +
+                   12 * (int64_t)st[ST_VISSLOTS] + 12 * (int64_t)st[ST_EVSLOTS] + 8 * (int64_t)st[ST_CHANGED] +
+                   8 * (int64_t)st[ST_CHSLOTS];
+}
+
+// Parameters of a maintenance launch pair from the handle: its buffers and
+// the schedule its options set (a captured step overrides the schedule).
+// The task queue must be allocated first (ensure_tasks).
+static MaintainParams handle_params(const cm_graph* h, int op) {
+    MaintainParams p{};
+    p.g = h->g;
+    p.g.n = h->n;
+    p.ctl = h->ctl;
+    p.R0 = h->R0;
+    p.R1 = h->R1;
+    p.VQ = h->VQ;
+    p.EQ = h->EQ;
+    p.CQ = h->CQ;
+    p.qmask = h->qmask;
+    p.op = op;
+    p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
+    p.small_edges = h->small_edges;
+    p.small_work = h->small_work;
+    p.big_work = h->big_work;
+    p.big_wave = h->big_work / 8 > 64 ? h->big_work / 8 : 64;
+    p.big_slots = 4 * p.big_work;
+    p.HQ = h->HQ;
+    p.TQ = h->TQ;
+    p.tqmask = h->tq_size - 1;
+    p.hub_len = h->hub_len;
+    p.block_len = op == CM_OP_INSERT ? h->block_len : h->block_len_del;
+    p.claim_max = h->claim_max;
+    p.sel_key = h->sel_key;
+    p.sel_rounds = h->sel_rounds;
+    return p;
+}
+
 // mode 0: maintain cores; mode 1: structure only (cores become stale).
 // per_graph (host, nullable): per-graph kept counts of a multi-graph batch.
 static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, int64_t* n_applied, int mode,
@@ -687,32 +745,9 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
             h->epoch = 1;
         }
         if ((rc = reset_launch_zone(h))) return rc;
-        MaintainParams p{};
-        p.g = h->g;
-        p.ctl = h->ctl;
-        p.R0 = h->R0;
-        p.R1 = h->R1;
-        p.VQ = h->VQ;
-        p.EQ = h->EQ;
-        p.CQ = h->CQ;
-        p.qmask = h->qmask;
-        p.op = op;
-        p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
-        p.max_iters = nrem0 + 1;
-        p.small_edges = h->small_edges;
-        p.small_work = h->small_work;
-        p.big_work = h->big_work;
-        p.big_wave = h->big_work / 8 > 64 ? h->big_work / 8 : 64;
-        p.big_slots = 4 * p.big_work;
         if ((rc = ensure_tasks(h))) return rc;
-        p.HQ = h->HQ;
-        p.TQ = h->TQ;
-        p.tqmask = h->tq_size - 1;
-        p.hub_len = h->hub_len;
-        p.block_len = op == CM_OP_INSERT ? h->block_len : h->block_len_del;
-        p.claim_max = h->claim_max;
-        p.sel_key = h->sel_key;
-        p.sel_rounds = h->sel_rounds;
+        MaintainParams p = handle_params(h, op);
+        p.max_iters = nrem0 + 1;
         int blocks, threads;
         persistent_geometry(h, 0, nrem0, &blocks, &threads);
         p.expect = (uint32_t)blocks;
@@ -763,32 +798,8 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         h->epoch = c.rs.epoch;
         float ms = 0;
         cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
-        cm_stats& s = h->last;
-        s.maintain_ms += ms;
-        s.iterations += (int64_t)c.st[ST_ITERS];
-        s.select_rounds += (int64_t)c.st[ST_ROUNDS];
-        s.selected += (int64_t)c.st[ST_SELECTED];
-        s.remaining_sum += (int64_t)c.st[ST_REMSUM];
-        s.visited += (int64_t)c.st[ST_VISITED];
-        s.visited_slots += (int64_t)c.st[ST_VISSLOTS];
-        s.evicted += (int64_t)c.st[ST_EVICTED];
-        s.evicted_slots += (int64_t)c.st[ST_EVSLOTS];
-        s.changed += (int64_t)c.st[ST_CHANGED];
-        s.changed_slots += (int64_t)c.st[ST_CHSLOTS];
-        s.waves += (int64_t)c.st[ST_WAVES];
-        s.barriers += (int64_t)c.st[ST_BARRIERS];
-        s.grid_iterations += (int64_t)c.st[ST_GRID_ITERS];
-        for (int i = 0; i < PH_COUNT && i < 7; i++) s.phase_ns[i] += (int64_t)c.ph[i];
-        // Algorithmic bytes of the maintenance launch: per iteration 16 B per
-        // remaining edge (pair + both cores) and 16 B per selected edge
-        // (claims, CSR writes); 16 B per visited vertex (its row) plus 12 B
-        // per slot (neighbour id, core, SD); 12 B per slot of an evicted
-        // vertex (id, core, support update); 8 B per changed vertex plus 8 B
-        // per slot (id, core) for the SD fix-up.
-        s.alg_bytes += 16 * (int64_t)c.st[ST_REMSUM] + 16 * (int64_t)c.st[ST_SELECTED] +
-                       16 * (int64_t)c.st[ST_VISITED] + 12 * (int64_t)c.st[ST_VISSLOTS] +
-                       12 * (int64_t)c.st[ST_EVSLOTS] + 8 * (int64_t)c.st[ST_CHANGED] +
-                       8 * (int64_t)c.st[ST_CHSLOTS];
+        h->last.maintain_ms += ms;
+        add_maintain_counters(h->last, c.st, c.ph);
     }
     if (op == CM_OP_DELETE) {
         h->idx_live -= nrem0;
@@ -1249,32 +1260,17 @@ static void step_release_graph(cm_step* s) {
 static MaintainParams step_params(const cm_step* s, int op, int* blocks, int* threads) {
     const cm_graph* h = s->h;
     const cm_step_config& c = s->cfg;
-    MaintainParams p{};
-    p.g = h->g;
-    p.g.n = h->n;
-    p.ctl = h->ctl;
-    p.R0 = h->R0;
-    p.R1 = h->R1;
-    p.VQ = h->VQ;
-    p.EQ = h->EQ;
-    p.CQ = h->CQ;
-    p.qmask = h->qmask;
-    p.op = op;
-    p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
+    MaintainParams p = handle_params(h, op);
     p.max_iters = (op == CM_OP_INSERT ? s->max_ins : s->max_del) + 1;
+    // the step's own schedule
     p.small_edges = c.block_mode_edges > 0 ? c.block_mode_edges : c.block_mode_edges < 0 ? 0 : 16384;
     p.small_work = c.block_mode_enter > 0 ? c.block_mode_enter : 1024;
     p.big_work = c.block_mode_leave > 0 ? c.block_mode_leave : 8192;
     p.big_wave = p.big_work / 8 > 64 ? p.big_work / 8 : 64;
     p.big_slots = 4 * p.big_work;
-    p.HQ = h->HQ;
-    p.TQ = h->TQ;
-    p.tqmask = h->tq_size - 1;
     p.hub_len = c.hub_slots > 0 ? (c.hub_slots < 128 ? 128 : c.hub_slots) : c.hub_slots < 0 ? 0 : 1024;
     p.block_len = op == CM_OP_INSERT ? (c.block_slots >= 32 ? c.block_slots : 4096) : h->block_len_del;
     p.claim_max = c.task_claim >= 1 && c.task_claim <= 8 ? c.task_claim : 1;
-    p.sel_key = h->sel_key;
-    p.sel_rounds = h->sel_rounds;
     int occ = maintain_blocks_per_sm(kGridThreadsHost);
     if (occ < 1) occ = 1;
     int bps = c.blocks_per_sm > 0 && c.blocks_per_sm < occ ? c.blocks_per_sm : occ;
@@ -1579,24 +1575,7 @@ static int step_finish(cm_step* s, const long long k[2], int64_t* applied[2]) {
             h->m -= kept;
         }
         st.applied += kept;
-        st.iterations += (int64_t)L.st[p][ST_ITERS];
-        st.select_rounds += (int64_t)L.st[p][ST_ROUNDS];
-        st.selected += (int64_t)L.st[p][ST_SELECTED];
-        st.remaining_sum += (int64_t)L.st[p][ST_REMSUM];
-        st.visited += (int64_t)L.st[p][ST_VISITED];
-        st.visited_slots += (int64_t)L.st[p][ST_VISSLOTS];
-        st.evicted += (int64_t)L.st[p][ST_EVICTED];
-        st.evicted_slots += (int64_t)L.st[p][ST_EVSLOTS];
-        st.changed += (int64_t)L.st[p][ST_CHANGED];
-        st.changed_slots += (int64_t)L.st[p][ST_CHSLOTS];
-        st.waves += (int64_t)L.st[p][ST_WAVES];
-        st.barriers += (int64_t)L.st[p][ST_BARRIERS];
-        st.grid_iterations += (int64_t)L.st[p][ST_GRID_ITERS];
-        for (int i = 0; i < PH_COUNT && i < 7; i++) st.phase_ns[i] += (int64_t)L.ph[p][i];
-        st.alg_bytes += 16 * (int64_t)L.st[p][ST_REMSUM] + 16 * (int64_t)L.st[p][ST_SELECTED] +
-                        16 * (int64_t)L.st[p][ST_VISITED] + 12 * (int64_t)L.st[p][ST_VISSLOTS] +
-                        12 * (int64_t)L.st[p][ST_EVSLOTS] + 8 * (int64_t)L.st[p][ST_CHANGED] +
-                        8 * (int64_t)L.st[p][ST_CHSLOTS];
+        add_maintain_counters(st, L.st[p], L.ph[p]);
         if (applied[p]) {
             if (h->dbases) {
                 for (int32_t i = 0; i < s->ng; i++) applied[p][i] = (int64_t)s->hPer[(size_t)p * s->ng + i];
