@@ -314,7 +314,7 @@ def run_sweep(args):
                     "frac": achieved / peak, "visited": st["visited"], "visited_slots": st["visited_slots"],
                     "evicted": st["evicted"], "evicted_slots": st["evicted_slots"], "changed": st["changed"],
                     "repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": levels,
-                    "peel_gbs": peel_gbs, "peel_frac": peel_gbs / peak, "peel_cascades": pst["waves"]})
+                    "peel_gbs": peel_gbs, "peel_frac": peel_gbs / peak, "peel_subwaves": pst["waves"]})
         cases.append(rec)
         print(json.dumps(rec), file=sys.stderr, flush=True)
     clocks = clk.stop()
@@ -894,7 +894,7 @@ def main():
         pk, _ = load_peaks()
         pgbs = pst["alg_bytes"] / (pst["maintain_ms"] / 1000.0) / 1e9 if pst["maintain_ms"] else 0.0
         repeel = {"repeel_ms": rp_ms, "maintain_insert_1e4_ms_median": mi, "speedup": rp_ms / mi,
-                  "peel_levels": pst["peel_levels"], "peel_cascades": pst["waves"],
+                  "peel_levels": pst["peel_levels"], "peel_subwaves": pst["waves"],
                   "peel_roofline": {"peel_and_sd_ms": pst["maintain_ms"], "alg_bytes": pst["alg_bytes"],
                                     "achieved_gbs": pgbs, "frac": pgbs / pk if pk else None}}
 

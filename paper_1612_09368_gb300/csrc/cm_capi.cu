@@ -564,9 +564,6 @@ static int peel_all(cm_graph* h) {
     p.F = h->OVL;
     p.qmask = h->qmask;
     p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
-    // the frontier ring starts all -1: the peel's cascades wait on an entry
-    // until its producer has written a vertex id there
-    CK(h, cudaMemsetAsync(h->OVL, 0xFF, (size_t)(h->qmask + 1) * sizeof(int32_t), h->stream));
     int blocks, threads;
     persistent_geometry(h, 1, h->n, &blocks, &threads);
     p.expect = (uint32_t)blocks;
@@ -577,7 +574,7 @@ static int peel_all(cm_graph* h) {
         return set_err(h, CM_ERR_LIMIT, "peeling stopped with device error %d", h->hctl->error);
     }
     h->last.peel_levels = (int64_t)h->hctl->st[ST_LEVELS];
-    h->last.waves = (int64_t)h->hctl->st[ST_WAVES];   // levels whose cascade ran
+    h->last.waves = (int64_t)h->hctl->st[ST_WAVES];   // sub-waves of the peel
     // Algorithmic bytes of the peel: 16 B per vertex to start it (degree
     // read, working degree, core and list writes); 16 B per remaining-list
     // entry scanned at a level (id, core, working degree, list write); 12 B

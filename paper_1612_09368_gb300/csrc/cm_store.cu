@@ -151,9 +151,6 @@ cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, cudaStream_t s) {
 // degree is <= k gets core k and leaves; each departure takes one degree
 // from every remaining neighbour, and neighbours that reach k leave at the
 // same level.  Empty levels are skipped to the smallest remaining degree.
-// Level whose cascade the block's poller found finished.
-__shared__ volatile long long s_level_done;
-
 __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
     Ctl* C = P.ctl;
     const DevGraph g = P.g;
@@ -162,8 +159,6 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
     bool ok;
-    if (threadIdx.x == 0) s_level_done = -1;
-    __syncthreads();
     // live vertices start unpeeled with their live degree
     for (long long base = gwarp * 32; base < g.n; base += nwarps * 32) {
         long long v = base + lane;
@@ -225,73 +220,25 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
             k = 0x7FFFFFFF - (int)smx;   // jump to the smallest remaining degree
             continue;
         }
-        // The level's cascade, without barriers.  Warps claim runs of
-        // frontier entries (the scan's, then the ones the cascade pushes),
-        // wait for each entry's producer to have written it, decrement its
-        // neighbours and push those that reach k.  A peeled neighbour needs
-        // no test: its working degree is at most k when it leaves and only
-        // falls after, so a decrement brings exactly k + 1 down to k only
-        // for a vertex still in the graph.  The level ends when every entry
-        // pushed has been processed: warps report what they processed before
-        // they wait, and one warp per block tests for that and tells the
-        // others through shared memory.  Entries are reset to -1 once read,
-        // so F is clean again for the next level.
-        {
-            const unsigned long long qcap = P.qmask + 1;
-            const unsigned long long run =
-                min(32ull, max(1ull, (fhi - f0) / ((unsigned long long)nwarps * 4ull)));
-            const bool poller = threadIdx.x < 32;
-            unsigned long long mine = 0;   // entries processed and not yet reported (lane 0)
-            const unsigned long long t_start = gtimer();
-            bool quit = false;
-            while (!quit) {
+        // sub-waves at level k.  A peeled neighbour needs no test: its
+        // working degree is at most k when it leaves and only falls after,
+        // so a decrement can bring exactly k + 1 down to k only for a
+        // vertex still in the graph.
+        unsigned long long lo = f0, hi = fhi;
+        while (hi > lo) {
+            const unsigned long long cnt = hi - lo;
+            // a warp takes a run of frontier vertices per claim: up to 32
+            // when the wave is wide (fewer claims on the shared counter),
+            // one when it is narrow (no warp left idle)
+            const unsigned long long run = min(32ull, max(1ull, cnt / ((unsigned long long)nwarps * 4ull)));
+            for (;;) {
                 unsigned long long j0 = 0;
                 if (lane == 0) j0 = atomicAdd(&C->pc[2], run);
                 j0 = __shfl_sync(0xffffffffu, j0, 0);
-                for (unsigned long long j = j0; j < j0 + run; j++) {
-                    const unsigned long long at = f0 + j;
-                    int v = -1, stop = 0;
-                    if (lane == 0) {
-                        unsigned int nap = 32;
-                        for (unsigned int spins = 0;; spins++) {
-                            if (at < qcap) {
-                                v = vload32(&P.F[at]);
-                                if (v >= 0) {
-                                    *(volatile int32_t*)&P.F[at] = -1;
-                                    break;
-                                }
-                            }
-                            if (mine) {   // report before waiting
-                                __threadfence();
-                                atomicAdd(&C->pc[0], mine);
-                                mine = 0;
-                            }
-                            if (poller) {
-                                const unsigned long long d = vload64(&C->pc[0]);   // done read first
-                                if (f0 + d == vload64(&C->tail[0]) || vload32(&C->error)) {
-                                    s_level_done = levels;
-                                    stop = 1;
-                                    break;
-                                }
-                            } else if (s_level_done == levels) {
-                                stop = 1;
-                                break;
-                            }
-                            if ((spins & 15u) == 0 && gtimer() - t_start > P.limit_ns) {
-                                atomicCAS(&C->error, 0, E_BARRIER_TIMEOUT);
-                                stop = 1;
-                                break;
-                            }
-                            __nanosleep(nap);
-                            if (nap < 512) nap <<= 1;
-                        }
-                    }
-                    stop = __shfl_sync(0xffffffffu, stop, 0);
-                    if (stop) {
-                        quit = true;
-                        break;
-                    }
-                    v = __shfl_sync(0xffffffffu, v, 0);
+                if (j0 >= cnt) break;
+                const unsigned long long j1 = min(cnt, j0 + run);
+                for (unsigned long long j = j0; j < j1; j++) {
+                    const int v = P.F[lo + j];
                     const long long o = g.off[v];
                     const int len = g.end[v];
                     slots += len;
@@ -313,13 +260,13 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
                             warp_push(&C->tail[0], P.F, ~0ull, p, w[q]);
                         }
                     }
-                    if (lane == 0) mine++;
                 }
             }
+            if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+            if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
+            lo = hi;
+            hi = vload64(&C->stail[0]);
         }
-        if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
-        unsigned long long hi = vload64(&C->stail[0]);
         ft = hi;
         k++;
         levels++;
