@@ -81,3 +81,33 @@ def test_ba_many_graphs_and_batches():
             io += ki
             do += kd
         assert io == len(w["ins"][r]) and do == len(w["dele"][r])
+
+
+def test_serving_trace_recipe():
+    """The serving trace keeps its stated recipe: Poisson arrivals at the
+    given rate, a uniform graph, 70% inserts, log-normal sizes with median
+    200 clamped to [10, 10^5]; inserts are absent distinct pairs, deletes
+    present distinct edges, and no edge belongs to two requests of a graph."""
+    from synth import workloads
+    n = 200000
+    e = synth.er(n, 2000000, synth.stream(77))
+    tr = workloads.serving_trace([(n, e), (n, e)], 2000.0, 1.0)
+    arr, gr, op, cnt = tr["arrival_ns"], tr["graph"], tr["op"], tr["counts"]
+    k = len(cnt)
+    assert abs(k - 2000) < 5 * 2000 ** 0.5                       # Poisson count
+    assert (np.diff(arr) >= 0).all() and arr[-1] < 1e9
+    assert abs((gr == 0).mean() - 0.5) < 0.05 and abs((op == 0).mean() - 0.7) < 0.05
+    assert cnt.min() >= 10 and cnt.max() <= 10 ** 5 and 150 < np.median(cnt) < 260
+    assert tr["off"][-1] == cnt.sum() and len(tr["edges"]) == cnt.sum()
+    have = set(((e[:, 0].astype(np.int64) << 32) | e[:, 1]).tolist())
+    have |= set(((e[:, 1].astype(np.int64) << 32) | e[:, 0]).tolist())
+    for g in (0, 1):
+        seen = set()
+        for j in np.nonzero(gr == g)[0]:
+            x = tr["edges"][tr["off"][j]:tr["off"][j + 1]].astype(np.int64)
+            keys = np.minimum(x[:, 0], x[:, 1]) << 32 | np.maximum(x[:, 0], x[:, 1])
+            ks = set(keys.tolist())
+            assert len(ks) == len(keys) and not (ks & seen)
+            seen |= ks
+            present = np.array([int(q) in have for q in keys])
+            assert present.all() if op[j] == 1 else not present.any()
