@@ -111,3 +111,39 @@ def test_serving_trace_recipe():
             seen |= ks
             present = np.array([int(q) in have for q in keys])
             assert present.all() if op[j] == 1 else not present.any()
+
+
+def test_rmat_rounds_recipe():
+    """Each round of the rounds workload, replayed on a plain edge set:
+    inserts are distinct absent pairs, deletes distinct present edges, new
+    vertices get ids in order and distinct live neighbours, deleted vertices
+    are live and take their edges with them; the replay ends on the
+    generator's own final graph."""
+    from synth import workloads
+    w = workloads.rmat_rounds(3, scale=12, ins=500, dele=500, vins=10, vdeg=8, vdel=10)
+    key = lambda u, v: (min(int(u), int(v)), max(int(u), int(v)))
+    edges = {key(u, v) for u, v in w.edges}
+    alive = set(range(w.n))
+    nxt = w.n
+    for r in w.rounds:
+        ins = [key(u, v) for u, v in r.ins]
+        assert len(set(ins)) == len(ins) and all(u != v and u in alive and v in alive for u, v in ins)
+        assert not (set(ins) & edges)
+        edges |= set(ins)
+        dl = [key(u, v) for u, v in r.dele]
+        assert len(set(dl)) == len(dl) and set(dl) <= edges
+        edges -= set(dl)
+        assert r.first_new_id == nxt
+        for i, nb in enumerate(r.vnbrs):
+            v = nxt + i
+            assert len(set(nb.tolist())) == len(nb) and all(int(x) in alive or nxt <= x < v for x in nb)
+            edges |= {key(v, x) for x in nb}
+        alive |= set(range(nxt, nxt + len(r.vnbrs)))
+        nxt += len(r.vnbrs)
+        before = len(edges)
+        for v in r.vdel.tolist():
+            assert v in alive
+            alive.discard(v)
+            edges = {e for e in edges if v not in e}
+        assert before - len(edges) == r.vdel_edges
+    assert edges == {key(u, v) for u, v in w.final.edges()}
