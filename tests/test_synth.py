@@ -147,3 +147,25 @@ def test_rmat_rounds_recipe():
             edges = {e for e in edges if v not in e}
         assert before - len(edges) == r.vdel_edges
     assert edges == {key(u, v) for u, v in w.final.edges()}
+
+
+def test_sweep_batch_laws():
+    """The sweep's batches: inserts are distinct absent pairs and deletes
+    distinct present edges under both endpoint laws.  Degree-proportional
+    insert endpoints have a far higher mean degree than uniform ones; for
+    deletes the "uniform" law picks a uniform vertex and then a uniform
+    neighbour (itself degree-biased), so the gap to uniform random edges is
+    smaller but still there."""
+    from synth import workloads
+    n, e, batches = workloads.rmat_sweep(scale=14, sizes=(3000,))
+    key = lambda a: set(map(tuple, np.sort(a, 1).tolist()))
+    have = key(e)
+    deg = np.bincount(e.ravel(), minlength=n)
+    mean_deg = {}
+    for (op, size, law), b in batches.items():
+        ks = key(b)
+        assert len(ks) == len(b) == size and (b[:, 0] != b[:, 1]).all()
+        assert (ks <= have) if op == "delete" else not (ks & have)
+        mean_deg[(op, law)] = deg[b.ravel()].mean()
+    assert mean_deg[("insert", synth.PREFERENTIAL)] > 4 * mean_deg[("insert", synth.UNIFORM)], mean_deg
+    assert mean_deg[("delete", synth.PREFERENTIAL)] > 1.1 * mean_deg[("delete", synth.UNIFORM)], mean_deg
