@@ -72,15 +72,17 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_traffic():
-    """DRAM bytes per launch of the maintenance kernel from the committed ncu
-    summary, only if the kernel source is unchanged since it was taken."""
+def kernel_traffic(workload: str):
+    """DRAM bytes per launch (one maintenance call) of the maintenance kernel
+    on `workload`, from the committed ncu summary, only if the kernel source
+    is unchanged since it was taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "maintain_traffic.json")) as f:
             t = json.load(f)
         if kernel_source_sha() != t.get("source_sha"):
             return None
-        return t.get("dram_bytes_per_launch")
+        w = t.get("workloads", {}).get(workload)
+        return None if w is None else w.get("dram_bytes_per_launch")
     except Exception:
         return None
 
@@ -240,98 +242,306 @@ def run_round(g, r, dev_inputs, cm):
     return a + b + c + d, st
 
 
+SWEEP_OPS = ("insert", "delete")
+SWEEP_LAWS = ((0, "uniform"), (1, "degree-proportional"))
+
+
+def sweep_cases(batches):
+    """The sweep's cases in a fixed order: by batch size, then operation,
+    then endpoint law."""
+    return sorted(batches.items(), key=lambda x: (x[0][1], SWEEP_OPS.index(x[0][0]), x[0][2]))
+
+
+def sweep_config(args, n, m, sizes, ops):
+    c = {"workload": f"rmat{args.scale}-sweep", "scale": args.scale, "edge_factor": 16,
+         "rmat_abcd": [0.57, 0.19, 0.19, 0.05], "vertices": n, "initial_edges": m, "batch_sizes": list(sizes),
+         "operations": list(ops), "laws": [nm for _, nm in SWEEP_LAWS],
+         "cases_per_step": len(sizes) * len(ops) * len(SWEEP_LAWS),
+         "step": "every case once: its batch applied by one maintenance call, then undone untimed",
+         "l2": "flushed before every timed call (256 MiB write)", "parallelism": "replicas"}
+    if handle_options(args):
+        c["options"] = handle_options(args)
+    return c
+
+
+def sweep_inputs(args):
+    from synth import workloads
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    ops = tuple(args.ops.split(","))
+    t0 = time.time()
+    n, e, batches = workloads.rmat_sweep(scale=args.scale, sizes=sizes, ops=ops)
+    return n, e, batches, sizes, ops, time.time() - t0
+
+
+def o3_law_rates(og, batches, sizes, ops, budget_s, offsets=None):
+    """The paper's sequential single-edge traversal (oracle O3) timed on a
+    prefix of the largest batch of every (operation, law), one edge per call,
+    until budget_s seconds per pair (at least one edge); the graph is put
+    back (structure undone, saved cores restored, untimed) after each.  O3
+    handles a batch one edge at a time, so its cost per edge depends on the
+    endpoint law and not on the batch size.  offsets: per pair, where in the
+    batch the prefix starts (the next call continues after it)."""
+    import oracle
+    c0 = og.cores()
+    out = {}
+    for op in ops:
+        for law, _ in SWEEP_LAWS:
+            b = batches[(op, max(sizes), law)]
+            start = 0 if offsets is None else offsets.get((op, law), 0) % len(b)
+            fwd = og.insert_edges if op == "insert" else og.delete_edges
+            done, t = 0, 0.0
+            while (done == 0 or t < budget_s) and start + done < len(b):
+                t0 = time.perf_counter()
+                fwd(b[start + done:start + done + 1])
+                t += time.perf_counter() - t0
+                done += 1
+            og.restore(oracle.DELETE if op == "insert" else oracle.INSERT, b[start:start + done], c0)
+            if offsets is not None:
+                offsets[(op, law)] = start + done
+            out[(op, law)] = (done, t)
+    return out
+
+
+def o3_estimate(rates, batches, sizes, ops):
+    """Edge updates/s the O3 traversal would reach on the whole sweep step:
+    every case's batch size over its (operation, law) rate, summed."""
+    edges = t = 0.0
+    for op in ops:
+        for law, _ in SWEEP_LAWS:
+            done, secs = rates[(op, law)]
+            for sz in sizes:
+                k = len(batches[(op, sz, law)])
+                edges += k
+                t += k * secs / done
+    return edges / t, t
+
+
 def run_sweep(args):
-    """R-MAT scale-24 batch sweep (the HBM-roofline workload): per operation,
-    batch size and endpoint law, the maintenance call and the full re-peel
-    comparator (structure update + GPU peeling), each undone untimed so
-    every case starts from the same graph."""
+    """R-MAT scale-24 batch sweep (the HBM-roofline workload, the default):
+    per batch size (10^3..10^6), operation and endpoint law (uniform or
+    degree-proportional), one maintenance call applies the batch (timed with
+    CUDA events on the handle's stream, L2 flushed before) and the batch is
+    undone untimed, so every case starts from the generated graph.  A step
+    is one pass over the 16 cases."""
     import torch
     import paper_1612_09368_gb300 as cm
     from paper_1612_09368_gb300 import build as libbuild
-    from synth import workloads
 
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
     libbuild.build()
-    sizes = tuple(int(x) for x in args.sizes.split(","))
-    t0 = time.time()
-    ops = tuple(args.ops.split(","))
-    n, e, batches = workloads.rmat_sweep(scale=args.scale, sizes=sizes, ops=ops)
-    gen_s = time.time() - t0
-    dev = torch.device("cuda", 0)
+    K, W = args.steps, args.warmup
+    n, e, batches, sizes, ops, gen_s = sweep_inputs(args)
+    cases = sweep_cases(batches)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     g = cm.CoreGraph(n, torch.from_numpy(e).to(dev), stream=stream, **handle_options(args))
     create = g.stats()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     peak, peak_kind = load_peaks()
-    cases = []
-    # untimed warm-up: one call of each operation, undone (the first calls
-    # of a handle size its task queue, index and batch buffers)
-    for (op, size, law), b in sorted(batches.items(), key=lambda x: (x[0][1], x[0][0], x[0][2]))[:4]:
-        db = torch.from_numpy(b).to(dev)
-        if op == "insert":
-            g.insert_edges(db)
-            g.delete_edges(db)
-        else:
-            g.delete_edges(db)
-            g.insert_edges(db)
-    torch.cuda.synchronize()
-    clk = ClockSampler(0)
-    clk.start()
-    for (op, size, law), b in sorted(batches.items(), key=lambda x: (x[0][1], x[0][0], x[0][2])):
-        db = torch.from_numpy(b).to(dev)
-        fwd = g.insert_edges if op == "insert" else g.delete_edges
-        inv = g.delete_edges if op == "insert" else g.insert_edges
-        rec = {"op": op, "batch": size, "law": "uniform" if law == 0 else "degree-proportional"}
-        ms, st = [], None
-        for rep in range(args.reps):
-            flush.fill_(rep)
+    dbat = [torch.from_numpy(b).to(dev) for _, b in cases]
+
+    def one_pass(timed_into=None, inputs=dbat):
+        for j, ((op, size, law), _) in enumerate(cases):
+            fwd = g.insert_edges if op == "insert" else g.delete_edges
+            inv = g.delete_edges if op == "insert" else g.insert_edges
+            flush.fill_(j)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            applied = fwd(db)
+            applied = fwd(inputs[j])
             a1.record(stream)
             a1.synchronize()
-            ms.append(a0.elapsed_time(a1))
             st = g.stats()
-            inv(db)
-        flush.fill_(7)
-        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        r0.record(stream)
-        g.apply_edges(cm.CM_OP_INSERT if op == "insert" else cm.CM_OP_DELETE, db)
-        g.recompute_cores()
-        r1.record(stream)
-        r1.synchronize()
-        rp = r0.elapsed_time(r1)
-        pst = g.stats()
-        levels = pst["peel_levels"]
-        peel_gbs = pst["alg_bytes"] / (pst["maintain_ms"] / 1000.0) / 1e9 if pst["maintain_ms"] else 0.0
-        g.apply_edges(cm.CM_OP_DELETE if op == "insert" else cm.CM_OP_INSERT, db)
-        g.recompute_cores()
-        call_ms = statistics.median(ms)
-        achieved = st["alg_bytes"] / (st["maintain_ms"] / 1000.0) / 1e9 if st["maintain_ms"] else 0.0
-        rec.update({"applied": applied, "call_ms": call_ms, "edge_updates_per_s": applied / (call_ms / 1000.0),
-                    "iterations": st["iterations"], "grid_iterations": st["grid_iterations"],
-                    "waves": st["waves"], "barriers": st["barriers"],
-                    "maintain_ms": st["maintain_ms"], "alg_bytes": st["alg_bytes"], "achieved_gbs": achieved,
-                    "frac": achieved / peak, "visited": st["visited"], "visited_slots": st["visited_slots"],
-                    "evicted": st["evicted"], "evicted_slots": st["evicted_slots"], "changed": st["changed"],
-                    "repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": levels,
-                    "peel_gbs": peel_gbs, "peel_frac": peel_gbs / peak, "peel_subwaves": pst["waves"]})
-        cases.append(rec)
-        print(json.dumps(rec), file=sys.stderr, flush=True)
+            if timed_into is not None:
+                timed_into.append((j, a0.elapsed_time(a1), applied, st))
+            inv(dbat[j])
+
+    for _ in range(W):
+        one_pass()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    torch.cuda.synchronize()
+    recs = []
+    step_ms = []
+    for s in range(K):
+        before = len(recs)
+        one_pass(recs)
+        step_ms.append(sum(r[1] for r in recs[before:]))
+    torch.cuda.synchronize()
     clocks = clk.stop()
-    best = max(cases, key=lambda c: c["frac"])
-    line = {"metric": METRIC, "workload": f"rmat{args.scale}-sweep", "unit": UNIT, "n_gpus": 1,
-            "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"rmat{args.scale}-sweep", "scale": args.scale, "edge_factor": 16,
-                       "options": handle_options(args),
-                       "vertices": n, "edges": int(len(e)), "batch_sizes": list(sizes),
-                       "laws": ["uniform", "degree-proportional"], "reps": args.reps,
-                       "l2": "flushed before every timed call (256 MiB write)"},
-            "peak": peak, "peak_kind": peak_kind, "clocks": clocks, "generation_s": gen_s,
-            "create_ms": create["call_ms"], "create_peel_levels": create["peel_levels"],
-            "best_roofline_case": {k: best[k] for k in ("op", "batch", "law", "achieved_gbs", "frac")},
-            "sweep": cases}
-    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+    t_ms = sum(step_ms)
+    units = sum(r[2] for r in recs)
+    t_ms_all, units_all = aggregate(t_ms, units, ws, dev)
+    value = units_all / (t_ms_all / 1000.0)
+    alg = sum(r[3]["alg_bytes"] for r in recs)
+    maint = sum(r[3]["maintain_ms"] for r in recs)
+    calls = sum(1 for r in recs if r[3]["maintain_ms"] > 0)
+    launches = sum(r[3]["launches"] for r in recs)
+    achieved = alg / (maint / 1000.0) / 1e9 if maint > 0 else 0.0
+
+    # e2e: the same pass through host (pinned) batches -- the library copies
+    # each in inside the timed call -- and the full core array read back to
+    # host memory at the end of the step
+    e2e = None
+    if not args.no_e2e:
+        hbat = [torch.from_numpy(b).pin_memory() for _, b in cases]
+        cores_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        e_ms, e_units = 0.0, 0
+        for _ in range(args.e2e_steps):
+            rec = []
+            one_pass(rec, inputs=hbat)
+            flush.fill_(99)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            g.cores(cores_h)
+            a1.record(stream)
+            a1.synchronize()
+            e_ms += sum(r[1] for r in rec) + a0.elapsed_time(a1)
+            e_units += sum(r[2] for r in rec)
+        e2e = {"value": e_units / (e_ms / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(b.numel() * 4 for b in hbat)),
+               "d2h_bytes_per_step": int(4 * n + 8 * len(cases)), "steps": args.e2e_steps,
+               "note": "host batches copied in by each call; the core array read back once per step"}
+
+    # per case: median call time over the timed steps, its roofline, and the
+    # re-peel comparator (apply the batch to the structure, full GPU peel)
+    per_case = []
+    for j, ((op, size, law), b) in enumerate(cases):
+        rs = [r for r in recs if r[0] == j]
+        call_ms = statistics.median(r[1] for r in rs)
+        st = rs[-1][3]
+        a_gbs = st["alg_bytes"] / (st["maintain_ms"] / 1000.0) / 1e9 if st["maintain_ms"] else 0.0
+        row = {"op": op, "batch": size, "law": SWEEP_LAWS[law][1], "applied": rs[-1][2], "call_ms": call_ms,
+               "call_ms_min": min(r[1] for r in rs), "call_ms_max": max(r[1] for r in rs),
+               "edge_updates_per_s": rs[-1][2] / (call_ms / 1000.0), "iterations": st["iterations"],
+               "grid_iterations": st["grid_iterations"], "maintain_ms": st["maintain_ms"],
+               "alg_bytes": st["alg_bytes"], "achieved_gbs": a_gbs, "frac": a_gbs / peak,
+               "visited_slots": st["visited_slots"], "evicted_slots": st["evicted_slots"],
+               "launches": st["launches"]}
+        if rank == 0 and not args.no_repeel:
+            flush.fill_(7)
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            g.apply_edges(cm.CM_OP_INSERT if op == "insert" else cm.CM_OP_DELETE, dbat[j])
+            g.recompute_cores()
+            r1.record(stream)
+            r1.synchronize()
+            rp = r0.elapsed_time(r1)
+            pst = g.stats()
+            pg = pst["alg_bytes"] / (pst["maintain_ms"] / 1000.0) / 1e9 if pst["maintain_ms"] else 0.0
+            g.apply_edges(cm.CM_OP_DELETE if op == "insert" else cm.CM_OP_INSERT, dbat[j])
+            g.recompute_cores()
+            row.update({"repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": pst["peel_levels"],
+                        "peel_ms": pst["maintain_ms"], "peel_alg_bytes": pst["alg_bytes"], "peel_gbs": pg,
+                        "peel_frac": pg / peak})
+        per_case.append(row)
+    repeel = None
+    if per_case and "repeel_ms" in per_case[0]:
+        pk = [r for r in per_case]
+        small = [r["speedup_vs_repeel"] for r in pk if r["batch"] <= 10 ** 4]
+        repeel = {"repeel_ms_median": statistics.median(r["repeel_ms"] for r in pk),
+                  "speedup_min_small_batches": min(small) if small else None,
+                  "speedup_median": statistics.median(r["speedup_vs_repeel"] for r in pk),
+                  "peel_roofline": {"peel_and_sd_ms": statistics.median(r["peel_ms"] for r in pk),
+                                    "alg_bytes": statistics.median(r["peel_alg_bytes"] for r in pk),
+                                    "achieved_gbs": statistics.median(r["peel_gbs"] for r in pk),
+                                    "frac": statistics.median(r["peel_frac"] for r in pk),
+                                    "levels": statistics.median(r["peel_levels"] for r in pk)}}
     g.close()
+    del dbat, flush
+    torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = sweep_cpu_baseline(args, n, e, batches, sizes, ops)
+
+    if rank == 0:
+        traffic = kernel_traffic(f"rmat{args.scale}-sweep")
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+                "ms_per_step": t_ms_all / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic", "config": sweep_config(args, n, int(len(e)), sizes, ops),
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                             "kernel": "maintain_kernel (grid and single-block launches of one maintenance call)",
+                             "launch_unit": "one maintenance call", "calls": calls,
+                             "alg_bytes_total": alg, "maintain_ms_total": maint,
+                             "alg_bytes_per_launch": alg / max(1, calls), "avg_launch_ms": maint / max(1, calls)},
+                "cpu_baseline": cpu, "repeel": repeel,
+                "detail": {"step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
+                                       "max": max(step_ms)},
+                           "generation_s": gen_s, "create_ms": create["call_ms"],
+                           "create_peel_levels": create["peel_levels"], "units": units_all, "cases": per_case}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def sweep_cpu_baseline(args, n, e, batches, sizes, ops):
+    """cpu_baseline of the sweep: oracle O3 on prefixes of every (operation,
+    law), extrapolated to the whole step (see o3_law_rates)."""
+    import oracle
+    og = oracle.OracleGraph(n, e, mode=oracle.SEQUENTIAL, simple=True)
+    per = max(0.5, args.cpu_budget / (len(ops) * len(SWEEP_LAWS)))
+    rates = o3_law_rates(og, batches, sizes, ops, per)
+    value, est_s = o3_estimate(rates, batches, sizes, ops)
+    sampled = {f"{op}/{SWEEP_LAWS[law][1]}": {"edges": d, "seconds": t, "edges_per_s": d / t}
+               for (op, law), (d, t) in rates.items()}
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle O3 (sequential single-edge traversal, 1 thread) on a prefix of the largest batch "
+                       f"of every operation and law, ~{per:.1f} s each (at least one edge), graph restored after "
+                       "each; the step's rate is every case's size over its (operation, law) rate, summed"),
+            "estimated_step_s": est_s, "sampled": sampled}
+
+
+def run_reference_sweep(args):
+    """--impl reference on the sweep: oracle O3 on the host, each step a
+    bounded sample of every (operation, law), continuing down the batch from
+    step to step; value = the step's edge updates/s extrapolated from the
+    sampled rates (o3_estimate), ms_per_step = the time actually spent."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    n, e, batches, sizes, ops, gen_s = sweep_inputs(args)
+    og = oracle.OracleGraph(n, e, mode=oracle.SEQUENTIAL, simple=True)
+    per = max(0.25, args.ref_budget / (len(ops) * len(SWEEP_LAWS)))
+    offsets = {}
+    pooled = {}
+    step_s = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = o3_law_rates(og, batches, sizes, ops, per, offsets)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            step_s.append(dt)
+            for k, (d, t) in r.items():
+                pd, pt = pooled.get(k, (0, 0.0))
+                pooled[k] = (pd + d, pt + t)
+    value, est_s = o3_estimate(pooled, batches, sizes, ops)
+    sample = (f"oracle O3 (sequential single-edge traversal, 1 thread): per step a prefix of the largest batch of "
+              f"every operation and law, ~{per:.2f} s each (at least one edge), continuing down the batch from step "
+              "to step, graph restored after each; value = the step's edge updates/s extrapolated from the "
+              "pooled rates (every case's size over its rate)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(step_s) / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": sweep_config(args, n, int(len(e)), sizes, ops),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "detail": {"estimated_full_step_s": est_s, "generation_s": gen_s,
+                       "sampled": {f"{op}/{SWEEP_LAWS[law][1]}": {"edges": d, "seconds": t}
+                                   for (op, law), (d, t) in pooled.items()}}}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -725,11 +935,11 @@ def run_paper_experiments(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 10 for the sweep, 100 rounds)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20-rounds", choices=["rmat20-rounds", "rmat24-sweep", "ba512-batched", "serving", "study",
-                                                              "paper-experiments"])
+    ap.add_argument("--workload", default="rmat24-sweep", choices=["rmat24-sweep", "rmat20-rounds", "ba512-batched",
+                                                                  "serving", "study", "paper-experiments"])
     ap.add_argument("--study-scales", dest="study_scales", default="15,17,19,21")
     ap.add_argument("--study-budget", dest="study_budget", type=float, default=3.0)
     ap.add_argument("--rates", default="500,1000,2000,4000,8000,16000")
@@ -740,18 +950,25 @@ def main():
     ap.add_argument("--options", default="", help="cm_options fields, e.g. block_slots=256,hub_slots=4096")
     ap.add_argument("--scale", type=int, default=None)
     ap.add_argument("--sizes", default="1000,10000,100000,1000000")
-    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--ops", default="insert,delete")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=20.0)
+    ap.add_argument("--ref-budget", dest="ref_budget", type=float, default=4.0,
+                    help="reference arm: seconds of O3 sampling per step")
+    ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-repeel", action="store_true")
     args = ap.parse_args()
     if args.scale is None:
         args.scale = {"rmat24-sweep": 24, "serving": 22}.get(args.workload, 20)
+    if args.steps is None:
+        args.steps = {"rmat24-sweep": 10, "rmat20-rounds": 100}.get(args.workload, 5)
     if args.impl == "reference":
-        return run_reference(args)
+        return run_reference_sweep(args) if args.workload == "rmat24-sweep" else run_reference(args)
     if args.workload == "rmat24-sweep":
         return run_sweep(args)
+    if args.workload == "rmat20-rounds":
+        return run_rounds(args)
     if args.workload == "ba512-batched":
         return run_batched(args)
     if args.workload == "serving":
@@ -760,7 +977,14 @@ def main():
         return run_study(args)
     if args.workload == "paper-experiments":
         return run_paper_experiments(args)
+    return 2
 
+
+def run_rounds(args):
+    """R-MAT scale-20 rounds (a secondary workload): each step is one round of
+    10^4 uniform new edges inserted, 10^4 uniform existing edges deleted,
+    100 vertices of degree 8 inserted and 100 uniform live vertices deleted,
+    each as one batched call."""
     import torch
     import paper_1612_09368_gb300 as cm
     from paper_1612_09368_gb300 import build as libbuild
@@ -837,7 +1061,8 @@ def main():
             iters.append(x["iterations"])
     torch.cuda.synchronize()
     clocks = clk.stop()
-    t_ms = sum(ev0[s].elapsed_time(ev1[s]) for s in range(K))
+    round_ms = [ev0[s].elapsed_time(ev1[s]) for s in range(K)]
+    t_ms = sum(round_ms)
     t_ms, units_all = aggregate(t_ms, units, ws, dev)
     value = units_all / (t_ms / 1000.0)
 
@@ -901,7 +1126,7 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (maint_ms / 1000.0) / 1e9 if maint_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": kernel_traffic(), "peak_kind": peak_kind,
+                "frac": achieved / peak, "traffic": kernel_traffic(w.name), "peak_kind": peak_kind,
                 "kernel": "maintain_kernel",
                 "alg_bytes_per_launch": alg_bytes / max(1, maint_launches),
                 "avg_launch_ms": maint_ms / max(1, maint_launches)}
@@ -928,7 +1153,9 @@ def main():
                            "grid_iterations": per_call_grid_it, "barriers": per_call_bar,
                            "volumes": per_call_vol,
                            "phase_ms": {k: v / 1e6 for k, v in phase_ns.items()},
-                           "maintain_ms_total": maint_ms, "units": units_all}}
+                           "maintain_ms_total": maint_ms, "units": units_all,
+                           "round_ms": {"min": min(round_ms), "median": statistics.median(round_ms),
+                                        "max": max(round_ms)}}}
         print(json.dumps(line), flush=True)
     g.close()
     if ws > 1:

@@ -195,6 +195,14 @@ int cm_delete_vertex(cm_graph* g, int32_t v);
  * cm_apply_edges without cm_recompute_cores). */
 int cm_get_cores(const cm_graph* g, int32_t* out, int32_t* n_total);
 
+/* Copies SD(v), the superior degree of Section IV, Definition 7 (the number
+ * of neighbours w with core(w) >= core(v)), of every vertex into out (host
+ * or device, n_total int32; dead vertices -1; NULL only queries the size).
+ * The library keeps SD with the cores: Algorithms 3 and 6 read it, and every
+ * update call leaves it consistent with the cores it returns.  Same errors
+ * as cm_get_cores. */
+int cm_get_superior_degrees(const cm_graph* g, int32_t* out, int32_t* n_total);
+
 /* Copies the current edge list (canonical pairs lo < hi, any order) into
  * host or device memory of capacity cap pairs; *m receives the edge count.
  * With cm_get_cores this is a complete checkpoint: cm_create(edges, cores)
@@ -411,7 +419,8 @@ void cm_server_destroy(cm_server* s);
  * array: calls whose work overlaps on the GPU (for example on two streams)
  * race on it and must not be issued.  The first call on a device looks up
  * the array's device address (once per device); make that first call
- * before any stream capture.
+ * before any stream capture.  Each call synchronises `stream` before it
+ * returns (it reads the kernel's error word back to the host).
  * Errors: CM_ERR_INVALID (n < 0, NULL or host pointers), CM_ERR_CAPACITY
  * (n > 1,048,576; nothing runs), CM_ERR_LIMIT (a bounded device wait ran
  * out), CM_ERR_CUDA. */

@@ -69,6 +69,9 @@ def load(plant: int = 0):
             "or_bz_trusted": (ctypes.c_int, [i32, i64, _i32p, _i32p]),
             "or_brute": (ctypes.c_int, [i32, i64, _i32p, _i32p]),
             "or_create": (vp, [i32, i64, _i32p, _i32p]),
+            "or_create_simple": (vp, [i32, i64, _i32p, _i32p]),
+            "or_apply_structure": (None, [vp, i32, _i32p, i64]),
+            "or_set_cores": (None, [vp, _i32p]),
             "or_free": (None, [vp]),
             "or_n": (i32, [vp]),
             "or_m": (i64, [vp]),
@@ -130,14 +133,17 @@ class OracleGraph:
     """Dynamic graph with core numbers maintained by O3 (mode 0) or O4 (mode 1)."""
 
     def __init__(self, n: int, edges, cores=None, mode: int = SUPERIOR, plant: int = 0,
-                 select_order: int = 0, select_rounds: int = 0):
+                 select_order: int = 0, select_rounds: int = 0, simple: bool = False):
         """select_order / select_rounds: the variants of reading R1 for O4
         (1 = canonical-key order instead of its fmix64; R > 0 = at most R
-        claim rounds per iteration)."""
+        claim rounds per iteration).  simple: the caller guarantees the edge
+        list is simple (no self-loop, no repeated pair), which skips the
+        per-edge membership test of construction (unchecked)."""
         self._L = load(plant)
         e = _e(edges)
         c = None if cores is None else np.ascontiguousarray(cores, dtype=np.int32)
-        self._h = self._L.or_create(n, len(e), _p32(e), None if c is None else _p32(c))
+        mk = self._L.or_create_simple if simple else self._L.or_create
+        self._h = mk(n, len(e), _p32(e), None if c is None else _p32(c))
         if not self._h:
             raise MemoryError("or_create")
         self.mode = mode
@@ -193,6 +199,18 @@ class OracleGraph:
     def delete_vertices(self, ids, mode=None) -> int:
         a = np.ascontiguousarray(ids, dtype=np.int32)
         return self._chk(self._L.or_delete_vertices(self._h, len(a), _p32(a), self.mode if mode is None else mode))
+
+    def restore(self, op: int, edges, cores) -> None:
+        """Puts the graph back into a saved state: applies `edges` to the
+        structure only (op INSERT adds them, DELETE removes them; each must
+        be absent, resp. present) and overwrites the cores with `cores`, the
+        saved core numbers of that state.  No maintenance runs."""
+        e = _e(edges)
+        c = np.ascontiguousarray(cores, dtype=np.int32)
+        if len(c) != self.n:
+            raise ValueError("cores must cover every vertex")
+        self._L.or_apply_structure(self._h, int(op), _p32(e), len(e))
+        self._L.or_set_cores(self._h, _p32(c))
 
     def last_iterations(self) -> int:
         return int(self._L.or_last_iterations(self._h))

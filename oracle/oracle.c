@@ -291,6 +291,50 @@ or_graph* or_create(int32_t n, int64_t m, const int32_t* edges, const int32_t* c
     return g;
 }
 
+void or_free(or_graph* g);
+
+/* The graph or_create builds, for an edge list already known to be simple
+ * (ids in range, no self-loop, no pair twice in either orientation), without
+ * or_create's per-edge membership test, which costs up to a hub's degree per
+ * edge on skewed graphs.  The precondition is NOT checked: a repeated pair
+ * would be stored twice.  Cores as in or_create (NULL: O1 on the graph). */
+or_graph* or_create_simple(int32_t n, int64_t m, const int32_t* edges, const int32_t* cores) {
+    if (n < 0 || m < 0) return NULL;
+    or_graph* g = (or_graph*)calloc(1, sizeof(or_graph));
+    if (!g) return NULL;
+    if (g_vgrow(g, n > 0 ? n : 1)) { free(g); return NULL; }
+    g->n = n;
+    for (int64_t i = 0; i < 2 * m; i++) {
+        if (edges[i] < 0 || edges[i] >= n) { or_free(g); return NULL; }
+        g->cap[edges[i]]++;
+    }
+    for (int32_t v = 0; v < n; v++) {
+        g->core[v] = 0;
+        if (g->cap[v] && !(g->adj[v] = (int32_t*)malloc((size_t)g->cap[v] * sizeof(int32_t)))) { or_free(g); return NULL; }
+    }
+    for (int64_t i = 0; i < m; i++) add_edge(g, edges[2 * i], edges[2 * i + 1]);
+    if (cores) {
+        for (int32_t v = 0; v < n; v++) g->core[v] = cores[v];
+    } else if (or_bz_trusted(n, m, edges, g->core) != OR_OK) {
+        or_free(g);
+        return NULL;
+    }
+    g->stamp = 1;
+    return g;
+}
+
+/* Checkpoint restore (no core maintenance): op 0 adds, op 1 removes the k
+ * pairs (each must be absent, resp. present, not checked) to the structure
+ * only; or_set_cores then overwrites every core number.  Used to put a graph
+ * back into a state saved before an update, whose core numbers are known. */
+void or_apply_structure(or_graph* g, int32_t op, const int32_t* e, int64_t k) {
+    for (int64_t i = 0; i < k; i++) {
+        if (op == 0) add_edge(g, e[2 * i], e[2 * i + 1]);
+        else del_edge(g, e[2 * i], e[2 * i + 1]);
+    }
+}
+void or_set_cores(or_graph* g, const int32_t* cores) { memcpy(g->core, cores, (size_t)g->n * sizeof(int32_t)); }
+
 void or_free(or_graph* g) {
     if (!g) return;
     for (int32_t i = 0; i < g->ncap; i++) free(g->adj[i]);

@@ -26,7 +26,7 @@ __all__ = [
     "CM_OP_INSERT", "CM_OP_DELETE", "CM_DEBUG_BARRIER_NEVER_RELEASES", "CoreMaintError", "cm_options", "cm_stats",
     "lib", "library_path", "cm_default_options", "cm_create", "cm_create_multi", "cm_destroy", "cm_insert_edges",
     "cm_delete_edges", "cm_insert_vertices", "cm_insert_vertex", "cm_delete_vertices", "cm_delete_vertex",
-    "cm_get_cores", "cm_get_edges", "cm_num_vertices", "cm_num_edges", "cm_apply_edges", "cm_recompute_cores",
+    "cm_get_cores", "cm_get_superior_degrees", "cm_get_edges", "cm_num_vertices", "cm_num_edges", "cm_apply_edges", "cm_recompute_cores",
     "cm_get_stats", "cm_set_stream", "cm_last_error", "cm_multi_bases", "cm_update_multi", "CoreGraph",
 ]
 
@@ -141,6 +141,7 @@ def lib():
             "cm_delete_vertex": (ctypes.c_int, [vp, i32]),
             "cm_get_cores": (ctypes.c_int, [vp, vp, p32]),
             "cm_get_edges": (ctypes.c_int, [vp, vp, i64, p64]),
+            "cm_get_superior_degrees": (ctypes.c_int, [vp, vp, p32]),
             "cm_num_vertices": (i32, [vp]),
             "cm_num_edges": (i64, [vp]),
             "cm_apply_edges": (ctypes.c_int, [vp, i32, vp, i64, p64]),
@@ -348,6 +349,19 @@ def cm_get_cores(h, out=None):
     return out
 
 
+def cm_get_superior_degrees(h, out=None):
+    """SD (Definition 7) of every vertex (dead -1) into `out` (a torch tensor,
+    host or CUDA) or a new numpy array."""
+    n = cm_num_vertices(h)
+    if out is None:
+        out = np.empty(n, dtype=np.int32)
+        _check(h, lib().cm_get_superior_degrees(h, ctypes.c_void_p(out.ctypes.data), None),
+               "cm_get_superior_degrees")
+        return out
+    _check(h, lib().cm_get_superior_degrees(h, ctypes.c_void_p(out.data_ptr()), None), "cm_get_superior_degrees")
+    return out
+
+
 def cm_get_edges(h) -> np.ndarray:
     m = cm_num_edges(h)
     out = np.empty((max(m, 0), 2), dtype=np.int32)
@@ -527,6 +541,9 @@ class CoreGraph:
 
     def cores(self, out=None):
         return cm_get_cores(self._h, out)
+
+    def superior_degrees(self, out=None):
+        return cm_get_superior_degrees(self._h, out)
 
     def edges(self) -> np.ndarray:
         return cm_get_edges(self._h)

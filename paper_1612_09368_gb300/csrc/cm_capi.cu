@@ -563,6 +563,9 @@ static int peel_all(cm_graph* h) {
     p.L1 = h->EQ;
     p.F = h->OVL;
     p.qmask = h->qmask;
+    // the hub-item ring is scratch outside a maintenance search
+    p.chunks = reinterpret_cast<unsigned long long*>(h->HQ);
+    p.chunk_cap = kHubRing * sizeof(HubItem) / sizeof(unsigned long long);
     p.limit_ns = (unsigned long long)h->opt.spin_limit_ns;
     int blocks, threads;
     persistent_geometry(h, 1, h->n, &blocks, &threads);
@@ -576,11 +579,11 @@ static int peel_all(cm_graph* h) {
     h->last.peel_levels = (int64_t)h->hctl->st[ST_LEVELS];
     h->last.waves = (int64_t)h->hctl->st[ST_WAVES];   // sub-waves of the peel
     // Algorithmic bytes of the peel: 16 B per vertex to start it (degree
-    // read, working degree, core and list writes); 16 B per remaining-list
-    // entry scanned at a level (id, core, working degree, list write); 12 B
-    // per adjacency slot of a peeled vertex (neighbour id, its core, the
-    // working-degree atomic).
-    h->last.alg_bytes += 16 * (int64_t)h->n + 16 * (int64_t)h->hctl->st[ST_VISITED] +
+    // read, working degree, core and list writes); 12 B per remaining-list
+    // entry scanned at a level (id, working degree, list write); 12 B per
+    // adjacency slot of a peeled vertex (neighbour id, the working-degree
+    // atomic, 4 B of its word when it leaves).
+    h->last.alg_bytes += 16 * (int64_t)h->n + 12 * (int64_t)h->hctl->st[ST_VISITED] +
                          12 * (int64_t)h->hctl->st[ST_VISSLOTS];
     return CM_OK;
 }
@@ -997,6 +1000,26 @@ extern "C" int cm_get_cores(const cm_graph* hc, int32_t* out, int32_t* n_total) 
         return CM_OK;
     }
     LAUNCH(h, export_cores(g, h->CQ, h->stream));   // CQ holds >= n entries
+    CK(h, cudaMemcpyAsync(out, h->CQ, (size_t)h->n * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return CM_OK;
+}
+
+extern "C" int cm_get_superior_degrees(const cm_graph* hc, int32_t* out, int32_t* n_total) {
+    cm_graph* h = const_cast<cm_graph*>(hc);
+    if (!h) return CM_ERR_INVALID;
+    if (h->poisoned) return set_err(h, CM_ERR_STATE, "handle poisoned: %s", h->err.c_str());
+    if (n_total) *n_total = h->n;
+    if (!out) return CM_OK;
+    if (h->cores_stale) return set_err(h, CM_ERR_STATE, "superior degrees are stale: call cm_recompute_cores");
+    DevGraph g = h->g;
+    g.n = h->n;
+    if (is_device_ptr(out)) {
+        LAUNCH(h, export_sd(g, out, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return CM_OK;
+    }
+    LAUNCH(h, export_sd(g, h->CQ, h->stream));   // CQ holds >= n entries
     CK(h, cudaMemcpyAsync(out, h->CQ, (size_t)h->n * 4, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return CM_OK;

@@ -54,6 +54,8 @@ struct PeelParams {
     int32_t* L1;
     int32_t* F;       // frontier ring [qmask+1]
     unsigned long long qmask;
+    unsigned long long* chunks;     // chunk tasks of high-degree frontier vertices
+    unsigned long long chunk_cap;
     uint32_t expect;
     uint32_t pad;
     unsigned long long limit_ns;
@@ -104,6 +106,7 @@ cudaError_t gather_incident(const int32_t* ids, int32_t count, DevGraph g, int32
 cudaError_t mark_dead(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s);
 cudaError_t pin_vertices(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s);
 cudaError_t export_cores(DevGraph g, int32_t* out, cudaStream_t s);
+cudaError_t export_sd(DevGraph g, int32_t* out, cudaStream_t s);
 cudaError_t export_edges(DevGraph g, int32_t* out, Ctl* c, cudaStream_t s);
 cudaError_t localize_multi(int32_t* E, long long k, const unsigned long long* kp, const long long* prefix,
                            const int32_t* bases, int32_t ng, cudaStream_t s);

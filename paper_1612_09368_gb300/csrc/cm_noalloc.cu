@@ -14,7 +14,8 @@
 // start at zero, and two calls whose work overlaps on the GPU (for example
 // on two streams) race on it.  The device address of the array is looked
 // up once per device, on the first call made with that device current;
-// make that first call before any stream capture.
+// make that first call before any stream capture.  Every call waits for its
+// stream (it reads the kernel's error word back) before it returns.
 #include <mutex>
 
 #include "../../include/coremaint.h"
@@ -170,6 +171,13 @@ static bool on_device(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// A failed runtime call: clear the error it left, so that a later
+// cudaGetLastError of the caller (or of a framework) does not report it.
+static int cuda_failed() {
+    cudaGetLastError();
+    return CM_ERR_CUDA;
+}
+
 }  // namespace cm
 
 using namespace cm;
@@ -186,12 +194,12 @@ extern "C" int cm_core_numbers_noalloc(int32_t n, const int64_t* row_off, const 
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     // the control block must start at zero; the per-vertex arrays are written before they are read
-    if (cudaMemsetAsync(scratch, 0, kCtlBytes, s) != cudaSuccess) return CM_ERR_CUDA;
+    if (cudaMemsetAsync(scratch, 0, kCtlBytes, s) != cudaSuccess) return cuda_failed();
     int dev = 0, sms = 0, occ = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return CM_ERR_CUDA;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CM_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_failed();
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cuda_failed();
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, peel_csr_kernel, 512, 0) != cudaSuccess || occ < 1)
-        return CM_ERR_CUDA;
+        return cuda_failed();
     int blocks = sms * occ;
     long long want = ((long long)n + 511) / 512;
     if (want < blocks) blocks = (int)(want > 0 ? want : 1);
@@ -205,11 +213,11 @@ extern "C" int cm_core_numbers_noalloc(int32_t n, const int64_t* row_off, const 
     p.limit_ns = 4000000000ull;
     void* args[] = {&p};
     if (cudaLaunchCooperativeKernel((const void*)peel_csr_kernel, dim3(blocks), dim3(512), args, 0, s) != cudaSuccess)
-        return CM_ERR_CUDA;
+        return cuda_failed();
     int err = 0;
     if (cudaMemcpyAsync(&err, &reinterpret_cast<Ctl*>(scratch)->error, sizeof(int), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-        return CM_ERR_CUDA;
+        return cuda_failed();
     return err ? CM_ERR_LIMIT : CM_OK;
 }

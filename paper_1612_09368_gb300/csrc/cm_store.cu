@@ -151,6 +151,46 @@ cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, cudaStream_t s) {
 // degree is <= k gets core k and leaves; each departure takes one degree
 // from every remaining neighbour, and neighbours that reach k leave at the
 // same level.  Empty levels are skipped to the smallest remaining degree.
+//
+// Working degrees only fall, one at a time, and a vertex leaves at level k
+// exactly when its degree reaches k (the decrement from k + 1 to k, or the
+// level's scan finding it at k).  So at the scan of level k every remaining
+// vertex has degree >= k and every vertex that left has degree < k: the
+// scan reads the working degree alone (never the 16-byte vertex word) to
+// tell the three cases apart.
+//
+// A frontier vertex with at least kPeelBig slots is not scanned by the warp
+// that claims it: its list is cut into kPeelChunk-slot chunk tasks that every
+// warp takes after a barrier, so one high-degree vertex does not hold a whole
+// sub-wave on a single warp.
+constexpr int kPeelBig = 2048;
+constexpr int kPeelChunk = 512;
+constexpr unsigned long long kPeelNoTask = ~0ull;
+
+// Slots [s0, s1) of the list at offset o (s0 a multiple of 4) at level k:
+// one degree off every neighbour; a neighbour that reaches k leaves now.
+// Four slots per lane per step with one 16-byte load (lists start 16-byte
+// aligned, capacities are multiples of 4).  Warp-collective.
+__device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& P, Ctl* C, long long o, int s0,
+                                           int s1, int k) {
+    const int lane = lane_id();
+    for (int base = s0; base < s1; base += 128) {
+        const int t0 = base + lane * 4;
+        int4 a = make_int4(HOLE, HOLE, HOLE, HOLE);
+        if (t0 < s1) a = __ldcs(reinterpret_cast<const int4*>(g.adj + o + t0));
+        const int w[4] = {a.x, t0 + 1 < s1 ? a.y : HOLE, t0 + 2 < s1 ? a.z : HOLE, t0 + 3 < s1 ? a.w : HOLE};
+        int r[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) r[q] = w[q] >= 0 ? atomicSub(&P.dcur[w[q]], 1) : 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const bool p = w[q] >= 0 && r[q] == k + 1;
+            if (p) g.hs[w[q]].x = k;
+            warp_push(&C->tail[0], P.F, ~0ull, p, w[q]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
     Ctl* C = P.ctl;
     const DevGraph g = P.g;
@@ -181,7 +221,8 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
     long long levels = 0;
     long long slots = 0;   // adjacency slots this warp scanned (algorithmic-byte counters)
     while (nl > 0) {
-        // scan the remaining list
+        // scan the remaining list: degree k leaves now, above k stays, below
+        // k left at an earlier level (dropped from the list)
         if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_VISITED] += nl;
         const unsigned long long f0 = ft;
         int mx = 0;   // max of (INT_MAX - degree) over survivors: gives the min degree
@@ -191,15 +232,13 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
             int v = 0;
             if (i < (long long)nl) {
                 v = Lc[i];
-                if (g.hs[v].x == UNPEELED) {
-                    int d = P.dcur[v];
-                    if (d <= k) {
-                        g.hs[v].x = k;
-                        peel = true;
-                    } else {
-                        keep = true;
-                        mx = max(mx, 0x7FFFFFFF - d);
-                    }
+                const int d = P.dcur[v];
+                if (d == k) {
+                    g.hs[v].x = k;
+                    peel = true;
+                } else if (d > k) {
+                    keep = true;
+                    mx = max(mx, 0x7FFFFFFF - d);
                 }
             }
             warp_push(&C->tail[0], P.F, ~0ull, peel, v);
@@ -242,27 +281,39 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
                     const long long o = g.off[v];
                     const int len = g.end[v];
                     slots += len;
-                    // four slots per lane per step, one 16-byte load (lists
-                    // start 16-byte aligned, capacities are multiples of 4)
-                    for (int base = 0; base < len; base += 128) {
-                        const int t0 = base + lane * 4;
-                        int4 a = make_int4(HOLE, HOLE, HOLE, HOLE);
-                        if (t0 < len) a = __ldcs(reinterpret_cast<const int4*>(g.adj + o + t0));
-                        const int w[4] = {a.x, t0 + 1 < len ? a.y : HOLE, t0 + 2 < len ? a.z : HOLE,
-                                          t0 + 3 < len ? a.w : HOLE};
-                        int r[4];
-#pragma unroll
-                        for (int q = 0; q < 4; q++) r[q] = w[q] >= 0 ? atomicSub(&P.dcur[w[q]], 1) : 0;
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const bool p = w[q] >= 0 && r[q] == k + 1;
-                            if (p) g.hs[w[q]].x = k;
-                            warp_push(&C->tail[0], P.F, ~0ull, p, w[q]);
+                    if (len >= kPeelBig) {
+                        // chunk tasks (vertex, chunk), run by every warp after the barrier
+                        const int nch = (len + kPeelChunk - 1) / kPeelChunk;
+                        unsigned long long tb = 0;
+                        if (lane == 0) tb = atomicAdd(&C->pc[3], (unsigned long long)nch);
+                        tb = __shfl_sync(0xffffffffu, tb, 0);
+                        const bool fits = tb + nch <= P.chunk_cap;
+                        for (int c = lane; c < nch; c += 32) {
+                            if (tb + c >= P.chunk_cap) break;
+                            P.chunks[tb + c] = fits ? (((unsigned long long)(uint32_t)v << 32) | (uint32_t)c)
+                                                    : kPeelNoTask;
                         }
+                        if (fits) continue;
                     }
+                    peel_range(g, P, C, o, 0, len, k);
                 }
             }
             if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+            const unsigned long long nchunks = min(vload64(&C->spc[3]), P.chunk_cap);
+            if (nchunks > 0) {
+                for (;;) {
+                    unsigned long long c = 0;
+                    if (lane == 0) c = atomicAdd(&C->pc[2], 1ull);
+                    c = __shfl_sync(0xffffffffu, c, 0);
+                    if (c >= nchunks) break;
+                    const unsigned long long task = P.chunks[c];
+                    if (task == kPeelNoTask) continue;
+                    const int v = (int)(task >> 32);
+                    const int s0 = (int)(task & 0xFFFFFFFFu) * kPeelChunk;
+                    peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k);
+                }
+                if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+            }
             if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
             lo = hi;
             hi = vload64(&C->stail[0]);
@@ -478,6 +529,14 @@ __global__ void export_cores_kernel(DevGraph g, int32_t* out) {
     out[v] = g.hs[v].x;
 }
 
+// SD (Definition 7) of every vertex; -1 for a deleted vertex.
+__global__ void export_sd_kernel(DevGraph g, int32_t* out) {
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n) return;
+    const int4 h = g.hs[v];
+    out[v] = h.x < 0 ? -1 : h.y;
+}
+
 __global__ void export_edges_kernel(DevGraph g, int2* out, Ctl* c) {
     long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -501,6 +560,11 @@ __global__ void export_edges_kernel(DevGraph g, int2* out, Ctl* c) {
 cudaError_t export_cores(DevGraph g, int32_t* out, cudaStream_t s) {
     if (g.n <= 0) return cudaSuccess;
     export_cores_kernel<<<grid_for(g.n, 256, 1ll << 31), 256, 0, s>>>(g, out);
+    return cudaGetLastError();
+}
+cudaError_t export_sd(DevGraph g, int32_t* out, cudaStream_t s) {
+    if (g.n <= 0) return cudaSuccess;
+    export_sd_kernel<<<grid_for(g.n, 256, 1ll << 31), 256, 0, s>>>(g, out);
     return cudaGetLastError();
 }
 cudaError_t export_edges(DevGraph g, int32_t* out, Ctl* c, cudaStream_t s) {

@@ -18,9 +18,12 @@ def test_traffic_applies_only_to_the_captured_kernel(monkeypatch):
     with open(os.path.join(bench.ROOT, "profiles", "maintain_traffic.json")) as f:
         stored = json.load(f)
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: stored["source_sha"])
-    assert bench.kernel_traffic() == stored["dram_bytes_per_launch"]
+    for name, w in stored["workloads"].items():
+        assert bench.kernel_traffic(name) == w["dram_bytes_per_launch"]
+    assert bench.kernel_traffic("no-such-workload") is None
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "0" * 16)
-    assert bench.kernel_traffic() is None
+    for name in stored["workloads"]:
+        assert bench.kernel_traffic(name) is None
 
 
 def test_options_parser():

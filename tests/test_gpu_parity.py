@@ -35,12 +35,26 @@ def _rand_graph(rng, n, p):
     return np.stack([iu[0][keep], iu[1][keep]], 1).astype(np.int32)
 
 
+def sd_recount(n, edges, cores):
+    """SD (Section IV, Definition 7) from scratch: for every vertex the number
+    of neighbours whose core is at least its own; -1 for dead vertices."""
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    cu, cv = cores[e[:, 0]], cores[e[:, 1]]
+    sd = np.bincount(e[:, 0][cv >= cu], minlength=n) + np.bincount(e[:, 1][cu >= cv], minlength=n)
+    return np.where(cores < 0, -1, sd).astype(np.int32)
+
+
 def _check_same(g, ref, what=""):
     gc = g.cores()
     rc = ref.cores()
     assert gc.shape == rc.shape, what
     bad = np.nonzero(gc != rc)[0]
     assert len(bad) == 0, f"{what}: {len(bad)} cores differ, first {bad[:8]} gpu {gc[bad[:8]]} ref {rc[bad[:8]]}"
+    # the superior degrees the library keeps beside the cores (Definition 7)
+    sd = g.superior_degrees()
+    exp = sd_recount(len(rc), ref.edges(), rc)
+    bad = np.nonzero(sd != exp)[0]
+    assert len(bad) == 0, f"{what}: {len(bad)} SD differ, first {bad[:8]} gpu {sd[bad[:8]]} recount {exp[bad[:8]]}"
 
 
 # ---------------------------------------------------------------- decomposition
@@ -265,6 +279,7 @@ def test_vertex_delete_hubs_and_neighbours(cm):
     assert (c[dead] == -1).all()
     alive = np.setdiff1d(np.arange(n), dead)
     assert (c[alive] == exp[alive]).all()
+    assert (g.superior_degrees() == sd_recount(n, e[keep], c)).all()
     assert g.stats()["iterations"] < deg[hubs[0]] // 4
     # the graph keeps working after it
     ref = oracle.OracleGraph(n, e[keep], mode=oracle.SUPERIOR)
@@ -489,7 +504,7 @@ def test_torch_allocator_and_device_outputs(cm):
 
 
 def test_readme_quick_start(cm):
-    """The README's example: a triangle with a pendant becomes K4 after two
+    """The quick-start example: a triangle with a pendant becomes K4 after two
     inserts (cores 3), then deleting vertex 3 leaves the triangle (cores 2)
     and a dead vertex (-1)."""
     import torch
