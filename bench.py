@@ -545,6 +545,22 @@ def run_reference_sweep(args):
     return 0
 
 
+def shard_workload(w, rank, world):
+    """The part of a many-graph workload (ba_many's dict) that one rank owns
+    under the library's partition of graphs over ranks."""
+    from paper_1612_09368_gb300.shard import partition, select
+    ms = np.diff(w["eoff"])
+    own = partition(ms, world)[rank]
+    _, edges = select(ms, w["edges"], own)
+    out = {"ns": w["ns"][own], "ms": w["ms"][own], "edges": edges,
+           "eoff": np.concatenate([[0], np.cumsum(ms[own])]).astype(np.int64),
+           "kins": w["kins"][:, own], "kdel": w["kdel"][:, own], "ins": [], "dele": []}
+    for r in range(len(w["ins"])):
+        out["ins"].append(select(w["kins"][r], w["ins"][r], own)[1])
+        out["dele"].append(select(w["kdel"][r], w["dele"][r], own)[1])
+    return out
+
+
 def run_batched(args):
     """512 independent Barabasi-Albert graphs, each with its own update batch
     (70% inserts, 30% deletes), applied by ONE captured step per round (one
@@ -557,16 +573,22 @@ def run_batched(args):
     from paper_1612_09368_gb300 import build as libbuild
     from synth import workloads
 
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     libbuild.build()
     K, W = args.steps, args.warmup
     ncmp = max(1, min(3, K))
     t0 = time.time()
     w = workloads.ba_many(args.graphs, rounds=W + K)
+    if ws > 1:   # independent graphs shard by graph: this rank keeps its own, no collective
+        w = shard_workload(w, rank, ws)
     gen_s = time.time() - t0
     ns, ms, eoff = w["ns"], w["ms"], w["eoff"]
     ng = len(ns)
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
     stream = torch.cuda.Stream(dev)
     peak, peak_kind = load_peaks()
     with torch.cuda.stream(stream):
@@ -668,15 +690,28 @@ def run_batched(args):
         untuned_value = float(np.mean([(kins[r].sum() + kdel[r].sum()) / (untuned_ms[r] / 1000.0)
                                        for r in range(W)]))
     achieved = alg / (maint_ms / 1000.0) / 1e9 if maint_ms > 0 else 0.0
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
-            "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    t_ms, units_all = aggregate(t_ms, applied, ws, dev)
+    value = units_all / (t_ms / 1000.0)
+    if ws > 1:
+        dist.destroy_process_group()
+        if rank != 0:
+            fwd.close()
+            inv.close()
+            g.close()
+            return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
+            "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"ba{ng}-batched", "graphs": ng, "vertices": int(ns.sum()),
+            "config": {"workload": f"ba{args.graphs}-batched", "graphs": args.graphs, "graphs_on_rank0": ng,
+                       "vertices": int(ns.sum()),
                        "initial_edges": int(eoff[-1]), "n_range": [int(ns.min()), int(ns.max())],
                        "attachment_range": [int(ms.min()), int(ms.max())],
                        "batch_per_round": int(kins[W:].sum() / K + kdel[W:].sum() / K),
                        "insert_fraction": 0.7, "l2": "flushed before every step (256 MiB write)",
-                       "parallelism": "one captured step per round"},
+                       "parallelism": "one captured step per round" if ws == 1 else
+                       f"graphs sharded over {ws} ranks (largest first onto the least-loaded rank), "
+                       "one captured step per round per rank, no collective"},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int((kins[W:W + ncmp].sum() + kdel[W:W + ncmp].sum()) * 8 / ncmp),
@@ -839,19 +874,33 @@ def run_study(args):
             else:
                 e = synth.rmat(sc, 4, seed)
             ins = synth.static_sample_insert(n, e, k, synth.UNIFORM, synth.stream(6, sc, 1, synth.INSERT))
+            # the deletes are edges of the generated graph (none of them inserted above)
             dele = synth.static_sample_delete(n, e, k, synth.PREFERENTIAL, synth.stream(6, sc, 1, synth.DELETE))
             g = cm.CoreGraph(n, torch.from_numpy(e).to(dev))
             c0 = g.cores()
             bi = bound(c0, ins)
             g.insert_edges(torch.from_numpy(ins).to(dev))
             si = g.stats()
-            bd = bound(g.cores(), dele)
+            c1 = g.cores()
+            bd = bound(c1, dele)
             g.delete_edges(torch.from_numpy(dele).to(dev))
             sd = g.stats()
+            c2 = g.cores()
             g.close()
+            # cores checked against O1 (Batagelj-Zaversnik) of the expected graphs
+            checked = n <= (1 << args.check_max_scale)
+            if checked:
+                e1 = np.concatenate([e, ins])
+                assert (c0 == oracle.bz(n, e, trusted=True)).all(), (fam, sc, "create")
+                assert (c1 == oracle.bz(n, e1, trusted=True)).all(), (fam, sc, "insert")
+                k1 = (np.minimum(e1[:, 0], e1[:, 1]).astype(np.int64) << 32) | np.maximum(e1[:, 0], e1[:, 1])
+                kd = (np.minimum(dele[:, 0], dele[:, 1]).astype(np.int64) << 32) | np.maximum(dele[:, 0], dele[:, 1])
+                e2 = e1[~np.isin(k1, kd)]
+                assert (c2 == oracle.bz(n, e2, trusted=True)).all(), (fam, sc, "delete")
             ri, ni = o3_rate(n, e, ins, 0, args.study_budget)
             rd, nd = o3_rate(n, e, dele, 1, args.study_budget)
             row = {"family": fam, "n": n, "edges": int(len(e)), "max_core": int(c0.max()),
+                   "cores_checked_against_o1": bool(checked),
                    "insert": {"gpu_ms": si["call_ms"], "iterations": si["iterations"], "first_bound": bi,
                               "o3_edges_per_s": ri, "o3_sample": ni,
                               "speedup_vs_o3": (k / ri * 1000.0) / si["call_ms"]},
@@ -890,9 +939,13 @@ def run_paper_experiments(args):
     dev = torch.device("cuda", 0)
     sc = args.scale
     n = 1 << sc
+    import oracle
     e = synth.rmat(sc, 16, synth.stream(7, 0, 0, synth.GRAPH))
     g = cm.CoreGraph(n, torch.from_numpy(e).to(dev))
     cores = g.cores()
+    check = sc <= args.check_max_scale
+    if check:
+        assert (cores == oracle.bz(n, e, trusted=True)).all(), "initial cores differ from O1"
     rng = np.random.default_rng(7)
 
     def cycle(sel):
@@ -903,6 +956,10 @@ def run_paper_experiments(args):
             st = g.stats()
             out[name] = {"edges": k, "call_ms": st["call_ms"], "us_per_edge": 1000.0 * st["call_ms"] / max(1, k),
                          "iterations": st["iterations"], "grid_iterations": st["grid_iterations"]}
+            if name == "delete" and check:   # the deleted state against O1 of the graph without them
+                keep = np.ones(len(e), bool)
+                keep[sel] = False
+                assert (g.cores() == oracle.bz(n, e[keep], trusted=True)).all(), "cores after the delete differ from O1"
         assert (g.cores() == cores).all(), "a delete then re-insert must restore every core"
         return out
 
@@ -926,6 +983,7 @@ def run_paper_experiments(args):
             "workload": "paper-experiments", "unit": "us/edge", "n_gpus": 1, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"rmat{sc}-paper-experiments", "scale": sc, "edge_factor": 16,
                        "vertices": n, "edges": int(len(e)), "max_core": int(cores.max()),
+                       "cores_checked_against_o1": bool(check),
                        "note": "R-MAT stands in for the paper's SNAP graphs; every case deletes then re-inserts"},
             "batch_size": size_rows, "core_distribution": core_rows}
     print(json.dumps(line), flush=True)
@@ -958,6 +1016,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-repeel", action="store_true")
+    ap.add_argument("--check-max-scale", dest="check_max_scale", type=int, default=22,
+                    help="study / paper-experiments: check cores against O1 up to 2^this many vertices")
     args = ap.parse_args()
     if args.scale is None:
         args.scale = {"rmat24-sweep": 24, "serving": 22}.get(args.workload, 20)

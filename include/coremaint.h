@@ -103,6 +103,14 @@ typedef struct cm_options {
  * one more block than exists, so each wait runs out after spin_limit_ns and
  * the call returns CM_ERR_LIMIT (no fault, no hang). */
 #define CM_DEBUG_BARRIER_NEVER_RELEASES 1
+/* Test hook: the next maintenance call may run one superior-edge-set
+ * iteration only; a batch that needs more stops with CM_ERR_LIMIT. */
+#define CM_DEBUG_ITER_CAP 2
+/* Test hook: the next maintenance call runs grid-wide and its search counts
+ * one task that is never queued, so the search never becomes quiescent:
+ * every warp's wait on the task queue runs out after spin_limit_ns and the
+ * call returns CM_ERR_LIMIT (no fault, no hang). */
+#define CM_DEBUG_TASK_WAIT_NEVER_ENDS 4
 
 /* Counters of the most recent update call (or of cm_recompute_cores). */
 typedef struct cm_stats {

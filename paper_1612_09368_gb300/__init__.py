@@ -23,7 +23,8 @@ from . import build as _build
 
 __all__ = [
     "CM_OK", "CM_ERR_INVALID", "CM_ERR_OOM", "CM_ERR_CAPACITY", "CM_ERR_LIMIT", "CM_ERR_CUDA", "CM_ERR_STATE",
-    "CM_OP_INSERT", "CM_OP_DELETE", "CM_DEBUG_BARRIER_NEVER_RELEASES", "CoreMaintError", "cm_options", "cm_stats",
+    "CM_OP_INSERT", "CM_OP_DELETE", "CM_DEBUG_BARRIER_NEVER_RELEASES", "CM_DEBUG_ITER_CAP",
+    "CM_DEBUG_TASK_WAIT_NEVER_ENDS", "CoreMaintError", "cm_options", "cm_stats",
     "lib", "library_path", "cm_default_options", "cm_create", "cm_create_multi", "cm_destroy", "cm_insert_edges",
     "cm_delete_edges", "cm_insert_vertices", "cm_insert_vertex", "cm_delete_vertices", "cm_delete_vertex",
     "cm_get_cores", "cm_get_superior_degrees", "cm_get_edges", "cm_num_vertices", "cm_num_edges", "cm_apply_edges", "cm_recompute_cores",
@@ -40,6 +41,8 @@ CM_ERR_STATE = -6
 CM_OP_INSERT = 0
 CM_OP_DELETE = 1
 CM_DEBUG_BARRIER_NEVER_RELEASES = 1
+CM_DEBUG_ITER_CAP = 2
+CM_DEBUG_TASK_WAIT_NEVER_ENDS = 4
 CM_SELECT_HASH = 0
 CM_SELECT_KEY = 1
 
@@ -470,13 +473,21 @@ def cm_step_destroy(s):
 class CoreGraph:
     """Owning wrapper: a graph resident on the GPU with maintained cores."""
 
-    def __init__(self, n, edges, cores=None, *, stream=None, use_torch_allocator=True, multi=None, **opts):
+    def __init__(self, n, edges, cores=None, *, stream=None, use_torch_allocator=True, multi=None, allocator=None,
+                 **opts):
+        """allocator: an object whose ``alloc`` / ``free`` attributes are the
+        cm_alloc_fn / cm_free_fn callbacks (kept alive by this wrapper);
+        otherwise torch's caching allocator (use_torch_allocator) or
+        cudaMalloc."""
         o = cm_default_options()
         for k, v in opts.items():
             setattr(o, k, v)
         self._alloc = None
-        if use_torch_allocator:
+        if allocator is not None:
+            self._alloc = allocator
+        elif use_torch_allocator:
             self._alloc = _TorchAllocator()
+        if self._alloc is not None:
             o.alloc = self._alloc.alloc
             o.free = self._alloc.free
         self.options = o

@@ -716,19 +716,31 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         CK(h, cudaStreamSynchronize(h->stream));
     }
     if (op == CM_OP_INSERT) {
-        h->idx_live += nrem0;
+        // Device memory the call may still need comes first: up to here
+        // ingest only counted pending insertions (need[]), so a failed
+        // allocation clears them and leaves the graph as it was.
+        auto undo_need = [&](int why) {
+            if (clear_need(h->R0, nrem0, nullptr, h->g, h->stream) != cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess) {
+                cudaGetLastError();
+                h->poisoned = true;
+            }
+            return why;
+        };
         const long long novl = (long long)c.noverflow;
         if (novl > 0) {
             LAUNCH(h, reloc_size(h->OVL, novl, nullptr, g, h->ctl, h->stream));
             if ((rc = rd_ctl(h))) return rc;
-            if ((rc = grow_pool(h, (long long)h->hctl->reloc_need))) {
-                h->poisoned = true;
-                return rc;
-            }
-            LAUNCH(h, relocate(h->OVL, novl, nullptr, h->g, h->ctl, h->stream));
+            if ((rc = grow_pool(h, (long long)h->hctl->reloc_need))) return undo_need(rc);
         }
+        // relocation moves lists without changing the graph
+        if (mode == 0 && nrem0 > 0 && (rc = ensure_tasks(h))) return undo_need(rc);
+        if (novl > 0) LAUNCH(h, relocate(h->OVL, novl, nullptr, h->g, h->ctl, h->stream));
+        h->idx_live += nrem0;
         LAUNCH(h, index_new_edges(h->R0, nrem0, nullptr, h->g, h->ctl, h->stream));
         LAUNCH(h, clear_need(h->R0, nrem0, nullptr, h->g, h->stream));
+    } else if (mode == 0 && nrem0 > 0 && (rc = ensure_tasks(h))) {
+        return rc;   // nothing changed yet
     }
     if (nrem0 > 0 && mode == 1) {
         LAUNCH(h, apply_structure(h->R0, nrem0, op, h->g, h->ctl, h->stream));
@@ -745,7 +757,6 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
             h->epoch = 1;
         }
         if ((rc = reset_launch_zone(h))) return rc;
-        if ((rc = ensure_tasks(h))) return rc;
         MaintainParams p = handle_params(h, op);
         p.max_iters = nrem0 + 1;
         int blocks, threads;
@@ -756,6 +767,15 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
             p.expect = (uint32_t)blocks + 1;   // test hook: no grid barrier can complete
             p.small_edges = -1;                // and the grid mode must run
             h->opt.debug_flags &= ~CM_DEBUG_BARRIER_NEVER_RELEASES;
+        }
+        if (h->opt.debug_flags & CM_DEBUG_ITER_CAP) {   // test hook: one iteration at most
+            p.max_iters = 1;
+            h->opt.debug_flags &= ~CM_DEBUG_ITER_CAP;
+        }
+        if (h->opt.debug_flags & CM_DEBUG_TASK_WAIT_NEVER_ENDS) {   // test hook: the search never quiesces
+            p.phantom_task = 1;
+            p.small_edges = -1;
+            h->opt.debug_flags &= ~CM_DEBUG_TASK_WAIT_NEVER_ENDS;
         }
         // where the call starts: all kept edges remain, in R0
         Resume rs{};
@@ -912,6 +932,11 @@ extern "C" int cm_insert_vertices(cm_graph* h, int32_t count, const int64_t* nbr
     rc = tot > 0 ? update_device(h, CM_OP_INSERT, h->dbatch, tot, &applied, 0, nullptr) : CM_OK;
     if (rc == CM_OK) {
         if (n_applied) *n_applied = applied;
+    } else if (rc == CM_ERR_OOM && !h->poisoned) {
+        // no edge of the new vertices went in: take the vertices back
+        // (their list space stays allocated in the pool, unused)
+        h->n = base;
+        h->g.n = base;
     } else {
         h->poisoned = true;   // the vertices exist but their edges failed
     }
@@ -966,6 +991,9 @@ extern "C" int cm_delete_vertices(cm_graph* h, int32_t count, const int32_t* ids
         // other vertices end with the cores of the graph without them;
         // a hub's edges then go in one iteration instead of one per
         // iteration.
+        // the call's last allocation before the graph changes: pinning and
+        // the deletions below allocate nothing
+        if ((rc = ensure_tasks(h))) break;
         h->launches++;
         if ((e = pin_vertices(dids, count, g, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "pin"); break; }
         if (k > 0 && (rc = update_device(h, CM_OP_DELETE, h->dbatch, k, &applied, 0, nullptr))) break;

@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     auto reset_tasks = [&]() {
         if (leader) {
             C->task_head = 0;
-            C->task_tail = 0;
+            C->task_tail = P.phantom_task ? 1 : 0;   // a phantom is never queued: no quiescence
             C->task_done = 0;
             C->hub_created = 0;
             C->hub_finished = 0;

@@ -43,6 +43,7 @@ struct MaintainParams {
     int32_t sel_key;          // selection order: 0 fmix64 of the canonical key, 1 the key itself
     int32_t sel_rounds;       // claim rounds per iteration (0 = until the set is maximal)
     int32_t use_cond;         // inside a captured step: the single-block kernel drives the loop node
+    int32_t phantom_task;     // test hook: every grid search counts one task that is never queued
     unsigned long long cond;  // that node's conditional handle
 };
 

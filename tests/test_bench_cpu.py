@@ -32,3 +32,33 @@ def test_options_parser():
     assert bench.handle_options(A()) == {"hub_slots": 512, "task_claim": 2}
     A.options = None
     assert bench.handle_options(A()) == {}
+
+
+def test_sweep_o3_estimate_weights_cases_by_size():
+    """The CPU baseline of the sweep extrapolates per (operation, law) rates
+    to every case: total edges over the sum of size / rate."""
+    import numpy as np
+    sizes = (10, 100)
+    batches = {(op, s, law): np.zeros((s, 2), np.int32) for op in bench.SWEEP_OPS for s in sizes
+               for law, _ in bench.SWEEP_LAWS}
+    rates = {("insert", 0): (10, 1.0), ("insert", 1): (1, 10.0), ("delete", 0): (100, 1.0), ("delete", 1): (50, 1.0)}
+    value, t = bench.o3_estimate(rates, batches, sizes, bench.SWEEP_OPS)
+    exp_t = 110 / 10.0 + 110 / 0.1 + 110 / 100.0 + 110 / 50.0
+    assert abs(t - exp_t) < 1e-9 and abs(value - 440 / exp_t) < 1e-9
+
+
+def test_sweep_o3_rates_restore_the_oracle_graph():
+    """o3_law_rates times O3 on batch prefixes and leaves the oracle graph
+    exactly as it found it (edges and cores)."""
+    import numpy as np
+    import oracle
+    from synth import workloads
+    n, e, batches = workloads.rmat_sweep(scale=12, sizes=(50, 200))
+    og = oracle.OracleGraph(n, e, mode=oracle.SEQUENTIAL, simple=True)
+    c0, m0 = og.cores(), og.m
+    offsets = {}
+    r = bench.o3_law_rates(og, batches, (50, 200), bench.SWEEP_OPS, 0.01, offsets)
+    assert set(r) == {(op, law) for op in bench.SWEEP_OPS for law, _ in bench.SWEEP_LAWS}
+    assert all(d >= 1 for d, t in r.values()) and all(offsets[k] == r[k][0] for k in r)
+    assert (og.cores() == c0).all() and og.m == m0
+    assert (og.cores() == oracle.bz(n, e)).all()
