@@ -424,8 +424,10 @@ def run_sweep(args):
                "edge_updates_per_s": rs[-1][2] / (call_ms / 1000.0), "iterations": st["iterations"],
                "grid_iterations": st["grid_iterations"], "maintain_ms": st["maintain_ms"],
                "alg_bytes": st["alg_bytes"], "achieved_gbs": a_gbs, "frac": a_gbs / peak,
-               "visited_slots": st["visited_slots"], "evicted_slots": st["evicted_slots"],
-               "launches": st["launches"]}
+               "visited": st["visited"], "visited_slots": st["visited_slots"], "evicted": st["evicted"],
+               "evicted_slots": st["evicted_slots"], "changed": st["changed"], "waves": st["waves"],
+               "select_rounds": st["select_rounds"], "launches": st["launches"],
+               "phase_ms": {k: v / 1e6 for k, v in st["phase_ns"].items()}}
         if rank == 0 and not args.no_repeel:
             flush.fill_(7)
             r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -440,6 +442,7 @@ def run_sweep(args):
             g.apply_edges(cm.CM_OP_DELETE if op == "insert" else cm.CM_OP_INSERT, dbat[j])
             g.recompute_cores()
             row.update({"repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": pst["peel_levels"],
+                        "peel_subwaves": pst["waves"],
                         "peel_ms": pst["maintain_ms"], "peel_alg_bytes": pst["alg_bytes"], "peel_gbs": pg,
                         "peel_frac": pg / peak})
         per_case.append(row)

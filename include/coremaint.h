@@ -67,7 +67,7 @@ typedef void (*cm_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 typedef struct cm_options {
     int32_t slack_pct;      /* per-vertex adjacency headroom in percent (default 25) */
     int32_t min_cap;        /* minimum adjacency slots per vertex, rounded up to 4 (default 4) */
-    int32_t block_threads;  /* threads per block of the peeling kernel (default 512) */
+    int32_t block_threads;  /* unused (kept for layout): every persistent kernel runs 512-thread blocks */
     int32_t blocks_per_sm;  /* resident blocks per SM of the persistent kernels; 0 = occupancy limit */
     int32_t max_sms;        /* SMs the persistent kernels may fill; 0 = all (lower it to share the GPU) */
     int32_t block_mode_edges; /* single-block mode only while at most this many edges remain (16384;

@@ -324,7 +324,7 @@ static int ensure_batch(cm_graph* h, long long k) {
 // as stay resident.  A small batch gets fewer blocks: grid barriers then
 // cost less, and there is not enough work for the whole GPU anyway.
 static void persistent_geometry(cm_graph* h, int kind, long long work, int* blocks, int* threads) {
-    int t = kind == 0 ? 512 : (h->opt.block_threads > 0 ? h->opt.block_threads : 512);   // maintenance blocks are 512 threads
+    const int t = 512;   // both persistent kernels run 512-thread blocks
     int occ = kind == 0 ? maintain_blocks_per_sm(t) : peel_blocks_per_sm(t);
     if (occ < 1) occ = 1;
     int bps = h->opt.blocks_per_sm > 0 ? (h->opt.blocks_per_sm < occ ? h->opt.blocks_per_sm : occ) : occ;

@@ -95,7 +95,10 @@ __global__ void set_cores_kernel(const int32_t* __restrict__ cores, DevGraph g) 
     g.hs[v].x = cores[v];
 }
 
-// SD(v), Definition 7: neighbours with core >= core(v).  Warp per vertex.
+// SD(v), Definition 7: neighbours with core >= core(v).  Warp per vertex;
+// four slots per lane per step with one 16-byte list load (lists start
+// 16-byte aligned and their capacity is a multiple of 4) and the four
+// neighbour gathers issued before any is used.
 __global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1) {
     long long w = v0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -105,9 +108,14 @@ __global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1) {
         if (k < 0) continue;
         long long o = g.off[w];
         int len = g.end[w], sd = 0;
-        for (int t = lane; t < len; t += 32) {
-            int x = g.adj[o + t];
-            if (x >= 0 && g.hs[x].x >= k) sd++;
+        for (int t0 = lane * 4; t0 < len; t0 += 128) {
+            const int4 a = __ldcs(reinterpret_cast<const int4*>(g.adj + o + t0));
+            const int x[4] = {a.x, t0 + 1 < len ? a.y : HOLE, t0 + 2 < len ? a.z : HOLE, t0 + 3 < len ? a.w : HOLE};
+            int c[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) c[q] = x[q] >= 0 ? g.hs[x[q]].x : -1;
+#pragma unroll
+            for (int q = 0; q < 4; q++) sd += c[q] >= k;
         }
         sd = warp_sum(sd);
         if (lane == 0) g.hs[w].y = sd;
@@ -160,19 +168,72 @@ cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, cudaStream_t s) {
 // tell the three cases apart.
 //
 // A frontier vertex with at least kPeelBig slots is not scanned by the warp
-// that claims it: its list is cut into kPeelChunk-slot chunk tasks that every
+// that takes it: its list is cut into kPeelChunk-slot chunk tasks that every
 // warp takes after a barrier, so one high-degree vertex does not hold a whole
 // sub-wave on a single warp.
+//
+// No counter is shared by the whole grid per vertex: the level scan
+// compacts a tile of kScanTile entries per block in shared memory and
+// appends it with one atomic per list; frontier vertices and chunk tasks
+// are dealt to warps by index, not claimed; and the vertices a sub-wave
+// peels collect in a per-warp shared buffer that reaches the frontier ring
+// with one atomic per flush.  (With one atomic per warp per step on a few
+// counters, the serialised atomics at those counters were most of the
+// peel's time.)
+constexpr int kPeelThreads = 512;
+constexpr int kPeelWarps = kPeelThreads / 32;
 constexpr int kPeelBig = 2048;
 constexpr int kPeelChunk = 512;
 constexpr unsigned long long kPeelNoTask = ~0ull;
+constexpr int kScanTile = 4 * kPeelThreads;   // list entries per block and scan step
+constexpr int kPushBuf = 256;                 // per-warp buffer of peeled vertices
+constexpr int kPushFlush = kPushBuf - 128;    // a scan step adds at most 128
+
+struct PeelShared {
+    int32_t keep[kScanTile];            // level scan: survivors of the tile
+    int32_t peel[kScanTile];            // level scan: vertices of degree k
+    int32_t buf[kPeelWarps][kPushBuf];  // sub-waves: peeled vertices per warp
+    int wcnt[kPeelWarps];
+    int nkeep, npeel, mx;
+    unsigned long long kbase, pbase, wbase;
+};
+
+// Appends the warp's buffered vertices to the frontier ring (one atomic).
+__device__ __forceinline__ void flush_peeled(Ctl* C, const PeelParams& P, int32_t* buf, int& cnt) {
+    if (cnt == 0) return;
+    unsigned long long b = 0;
+    if (lane_id() == 0) b = atomicAdd(&C->tail[0], (unsigned long long)cnt);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    for (int i = lane_id(); i < cnt; i += 32) P.F[b + i] = buf[i];
+    __syncwarp();
+    cnt = 0;
+}
+
+// End of a sub-wave: the block's warps append their buffers to the frontier
+// ring together, with one atomic.  Every thread of the block calls it.
+__device__ __forceinline__ void block_flush_peeled(Ctl* C, const PeelParams& P, PeelShared& S, int& cnt) {
+    const int wib = threadIdx.x >> 5;
+    if (lane_id() == 0) S.wcnt[wib] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int i = 0; i < kPeelWarps; i++) tot += S.wcnt[i];
+        S.wbase = tot ? atomicAdd(&C->tail[0], (unsigned long long)tot) : 0;
+    }
+    __syncthreads();
+    int pre = 0;
+    for (int i = 0; i < wib; i++) pre += S.wcnt[i];
+    for (int i = lane_id(); i < cnt; i += 32) P.F[S.wbase + pre + i] = S.buf[wib][i];
+    cnt = 0;
+}
 
 // Slots [s0, s1) of the list at offset o (s0 a multiple of 4) at level k:
-// one degree off every neighbour; a neighbour that reaches k leaves now.
-// Four slots per lane per step with one 16-byte load (lists start 16-byte
-// aligned, capacities are multiples of 4).  Warp-collective.
+// one degree off every neighbour; a neighbour that reaches k leaves now and
+// goes to the warp's buffer.  Four slots per lane per step with one 16-byte
+// load (lists start 16-byte aligned, capacities are multiples of 4).
+// Warp-collective.
 __device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& P, Ctl* C, long long o, int s0,
-                                           int s1, int k) {
+                                           int s1, int k, int32_t* buf, int& cnt) {
     const int lane = lane_id();
     for (int base = s0; base < s1; base += 128) {
         const int t0 = base + lane * 4;
@@ -182,35 +243,69 @@ __device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& 
         int r[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) r[q] = w[q] >= 0 ? atomicSub(&P.dcur[w[q]], 1) : 0;
+        int mine = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) mine += w[q] >= 0 && r[q] == k + 1;
+        if (!__any_sync(0xffffffffu, mine != 0)) continue;
+        int incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        int at = cnt + incl - mine;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const bool p = w[q] >= 0 && r[q] == k + 1;
-            if (p) g.hs[w[q]].x = k;
-            warp_push(&C->tail[0], P.F, ~0ull, p, w[q]);
+            if (w[q] >= 0 && r[q] == k + 1) {
+                g.hs[w[q]].x = k;
+                buf[at++] = w[q];
+            }
         }
+        cnt += __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        if (cnt > kPushFlush) flush_peeled(C, P, buf, cnt);
     }
 }
 
-__global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
+__global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
     Ctl* C = P.ctl;
     const DevGraph g = P.g;
+    __shared__ PeelShared S;
     const int lane = lane_id();
+    const int wib = threadIdx.x >> 5;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
+    int32_t* buf = S.buf[wib];
+    int cnt = 0;
     bool ok;
-    // live vertices start unpeeled with their live degree
-    for (long long base = gwarp * 32; base < g.n; base += nwarps * 32) {
-        long long v = base + lane;
-        bool live = false;
-        if (v < g.n) {
-            live = g.hs[v].x != -1;
-            if (live) {
-                P.dcur[v] = g.deg[v];
-                g.hs[v].x = UNPEELED;
+    // live vertices start unpeeled with their live degree (compacted into
+    // the remaining list a tile at a time, like the level scans below)
+    for (long long t0 = (long long)blockIdx.x * kScanTile; t0 < g.n; t0 += (long long)gridDim.x * kScanTile) {
+        if (threadIdx.x == 0) S.nkeep = 0;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const long long v = t0 + q * kPeelThreads + threadIdx.x;
+            bool live = false;
+            if (v < g.n) {
+                live = g.hs[v].x != -1;
+                if (live) {
+                    P.dcur[v] = g.deg[v];
+                    g.hs[v].x = UNPEELED;
+                }
             }
+            const unsigned lb = __ballot_sync(0xffffffffu, live);
+            int kp = 0;
+            if (lane == 0 && lb) kp = atomicAdd(&S.nkeep, __popc(lb));
+            kp = __shfl_sync(0xffffffffu, kp, 0);
+            if (live) S.keep[kp + __popc(lb & ((1u << lane) - 1))] = (int32_t)v;
         }
-        warp_push(&C->pc[1], P.L0, ~0ull, live, (int32_t)v);
+        __syncthreads();
+        if (threadIdx.x == 0) S.kbase = S.nkeep ? atomicAdd(&C->pc[1], (unsigned long long)S.nkeep) : 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < S.nkeep; j += kPeelThreads) P.L0[S.kbase + j] = S.keep[j];
+        __syncthreads();
     }
     if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
     unsigned long long nl = vload64(&C->spc[1]);
@@ -221,31 +316,60 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
     long long levels = 0;
     long long slots = 0;   // adjacency slots this warp scanned (algorithmic-byte counters)
     while (nl > 0) {
-        // scan the remaining list: degree k leaves now, above k stays, below
-        // k left at an earlier level (dropped from the list)
+        // scan the remaining list, one tile per block at a time: degree k
+        // leaves now, above k stays, below k left at an earlier level
         if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_VISITED] += nl;
         const unsigned long long f0 = ft;
-        int mx = 0;   // max of (INT_MAX - degree) over survivors: gives the min degree
-        for (long long base = gwarp * 32; base < (long long)nl; base += nwarps * 32) {
-            long long i = base + lane;
-            bool peel = false, keep = false;
-            int v = 0;
-            if (i < (long long)nl) {
-                v = Lc[i];
-                const int d = P.dcur[v];
-                if (d == k) {
-                    g.hs[v].x = k;
-                    peel = true;
-                } else if (d > k) {
-                    keep = true;
-                    mx = max(mx, 0x7FFFFFFF - d);
-                }
+        for (long long t0 = (long long)blockIdx.x * kScanTile; t0 < (long long)nl;
+             t0 += (long long)gridDim.x * kScanTile) {
+            if (threadIdx.x == 0) {
+                S.nkeep = 0;
+                S.npeel = 0;
+                S.mx = 0;
             }
-            warp_push(&C->tail[0], P.F, ~0ull, peel, v);
-            warp_push(&C->pc[1], Ln, ~0ull, keep, v);
+            __syncthreads();
+            int mx = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const long long i = t0 + q * kPeelThreads + threadIdx.x;
+                bool peel = false, keep = false;
+                int v = 0;
+                if (i < (long long)nl) {
+                    v = Lc[i];
+                    const int d = P.dcur[v];
+                    if (d == k) {
+                        g.hs[v].x = k;
+                        peel = true;
+                    } else if (d > k) {
+                        keep = true;
+                        mx = max(mx, 0x7FFFFFFF - d);
+                    }
+                }
+                const unsigned kb = __ballot_sync(0xffffffffu, keep), pb = __ballot_sync(0xffffffffu, peel);
+                int kp = 0, pp = 0;
+                if (lane == 0) {
+                    if (kb) kp = atomicAdd(&S.nkeep, __popc(kb));
+                    if (pb) pp = atomicAdd(&S.npeel, __popc(pb));
+                }
+                kp = __shfl_sync(0xffffffffu, kp, 0);
+                pp = __shfl_sync(0xffffffffu, pp, 0);
+                const unsigned below = (1u << lane) - 1;
+                if (keep) S.keep[kp + __popc(kb & below)] = v;
+                if (peel) S.peel[pp + __popc(pb & below)] = v;
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0 && mx) atomicMax(&S.mx, mx);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                S.kbase = S.nkeep ? atomicAdd(&C->pc[1], (unsigned long long)S.nkeep) : 0;
+                S.pbase = S.npeel ? atomicAdd(&C->tail[0], (unsigned long long)S.npeel) : 0;
+                if (S.mx) atomicMax(&C->pc[3], (unsigned long long)S.mx);
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < S.nkeep; j += kPeelThreads) Ln[S.kbase + j] = S.keep[j];
+            for (int j = threadIdx.x; j < S.npeel; j += kPeelThreads) P.F[S.pbase + j] = S.peel[j];
+            __syncthreads();
         }
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0 && mx) atomicMax(&C->pc[3], (unsigned long long)mx);
         if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
         unsigned long long fhi = vload64(&C->stail[0]);
         unsigned long long nln = vload64(&C->spc[1]);
@@ -265,53 +389,40 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
         // vertex still in the graph.
         unsigned long long lo = f0, hi = fhi;
         while (hi > lo) {
-            const unsigned long long cnt = hi - lo;
-            // a warp takes a run of frontier vertices per claim: up to 32
-            // when the wave is wide (fewer claims on the shared counter),
-            // one when it is narrow (no warp left idle)
-            const unsigned long long run = min(32ull, max(1ull, cnt / ((unsigned long long)nwarps * 4ull)));
-            for (;;) {
-                unsigned long long j0 = 0;
-                if (lane == 0) j0 = atomicAdd(&C->pc[2], run);
-                j0 = __shfl_sync(0xffffffffu, j0, 0);
-                if (j0 >= cnt) break;
-                const unsigned long long j1 = min(cnt, j0 + run);
-                for (unsigned long long j = j0; j < j1; j++) {
-                    const int v = P.F[lo + j];
-                    const long long o = g.off[v];
-                    const int len = g.end[v];
-                    slots += len;
-                    if (len >= kPeelBig) {
-                        // chunk tasks (vertex, chunk), run by every warp after the barrier
-                        const int nch = (len + kPeelChunk - 1) / kPeelChunk;
-                        unsigned long long tb = 0;
-                        if (lane == 0) tb = atomicAdd(&C->pc[3], (unsigned long long)nch);
-                        tb = __shfl_sync(0xffffffffu, tb, 0);
-                        const bool fits = tb + nch <= P.chunk_cap;
-                        for (int c = lane; c < nch; c += 32) {
-                            if (tb + c >= P.chunk_cap) break;
-                            P.chunks[tb + c] = fits ? (((unsigned long long)(uint32_t)v << 32) | (uint32_t)c)
-                                                    : kPeelNoTask;
-                        }
-                        if (fits) continue;
+            const unsigned long long cnt_f = hi - lo;
+            for (unsigned long long j = (unsigned long long)gwarp; j < cnt_f; j += (unsigned long long)nwarps) {
+                const int v = P.F[lo + j];
+                const long long o = g.off[v];
+                const int len = g.end[v];
+                slots += len;
+                if (len >= kPeelBig) {
+                    // chunk tasks (vertex, chunk), run by every warp after the barrier
+                    const int nch = (len + kPeelChunk - 1) / kPeelChunk;
+                    unsigned long long tb = 0;
+                    if (lane == 0) tb = atomicAdd(&C->pc[3], (unsigned long long)nch);
+                    tb = __shfl_sync(0xffffffffu, tb, 0);
+                    const bool fits = tb + nch <= P.chunk_cap;
+                    for (int c = lane; c < nch; c += 32) {
+                        if (tb + c >= P.chunk_cap) break;
+                        P.chunks[tb + c] = fits ? (((unsigned long long)(uint32_t)v << 32) | (uint32_t)c)
+                                                : kPeelNoTask;
                     }
-                    peel_range(g, P, C, o, 0, len, k);
+                    if (fits) continue;
                 }
+                peel_range(g, P, C, o, 0, len, k, buf, cnt);
             }
+            block_flush_peeled(C, P, S, cnt);
             if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
             const unsigned long long nchunks = min(vload64(&C->spc[3]), P.chunk_cap);
             if (nchunks > 0) {
-                for (;;) {
-                    unsigned long long c = 0;
-                    if (lane == 0) c = atomicAdd(&C->pc[2], 1ull);
-                    c = __shfl_sync(0xffffffffu, c, 0);
-                    if (c >= nchunks) break;
+                for (unsigned long long c = (unsigned long long)gwarp; c < nchunks; c += (unsigned long long)nwarps) {
                     const unsigned long long task = P.chunks[c];
                     if (task == kPeelNoTask) continue;
                     const int v = (int)(task >> 32);
                     const int s0 = (int)(task & 0xFFFFFFFFu) * kPeelChunk;
-                    peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k);
+                    peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k, buf, cnt);
                 }
+                block_flush_peeled(C, P, S, cnt);
                 if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
@@ -326,16 +437,20 @@ __global__ void __launch_bounds__(512) peel_kernel(PeelParams P) {
     if (lane == 0 && slots) atomicAdd(&C->st[ST_VISSLOTS], (unsigned long long)slots);
 }
 
+// The peel always runs kPeelThreads-thread blocks (its tiles and per-warp
+// buffers are laid out for them); `threads` is ignored.
 int peel_blocks_per_sm(int threads) {
+    (void)threads;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, peel_kernel, threads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, peel_kernel, kPeelThreads, 0) != cudaSuccess) return 0;
     return nb;
 }
 
 cudaError_t launch_peel(const PeelParams& p, int blocks, int threads, cudaStream_t s) {
+    (void)threads;
     PeelParams q = p;
     void* args[] = {&q};
-    return cudaLaunchCooperativeKernel((const void*)peel_kernel, dim3(blocks), dim3(threads), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)peel_kernel, dim3(blocks), dim3(kPeelThreads), args, 0, s);
 }
 
 // ------------------------------------------------------------------ index rehash

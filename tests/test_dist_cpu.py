@@ -35,7 +35,7 @@ def _rank_main(rank, world, port, out):
 
 
 def test_two_rank_aggregation_gloo():
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     port = 29000 + os.getpid() % 1000
     mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
@@ -94,7 +94,7 @@ def test_sharded_graphs_two_ranks_gloo():
     import oracle
     from paper_1612_09368_gb300 import shard
     from synth import workloads
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     port = 29500 + os.getpid() % 1000
     mp.spawn(_shard_main, args=(2, port, out), nprocs=2, join=True)
