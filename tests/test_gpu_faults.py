@@ -97,7 +97,7 @@ def test_allocation_failure_leaves_the_graph_unchanged(cm):
             alloc = FailingAllocator(cm)
             g = cm.CoreGraph(n, e, allocator=alloc)
             ref = oracle.OracleGraph(n, e, mode=oracle.SUPERIOR)
-            for _, prev, prev_ref in ops[:j]:       # the state the op starts from
+            for _, prev, prev_ref, _ in ops[:j]:    # the state the op starts from
                 prev(g)
                 prev_ref(ref)
             before = _state(g)
