@@ -73,7 +73,8 @@ def test_allocation_failure_leaves_the_graph_unchanged(cm):
     ins = synth.static_sample_insert(n, e, 20000, synth.PREFERENTIAL, synth.stream(80, 0, 0, synth.INSERT))
     dele = synth.static_sample_delete(n, e, 4000, synth.PREFERENTIAL, synth.stream(80, 0, 0, synth.DELETE))
     rng = np.random.default_rng(80)
-    vnb = [rng.choice(n, 12, replace=False).tolist() for _ in range(300)]
+    nv = 2500            # more new vertices than the vertex arrays' headroom: they must grow
+    vnb = [rng.choice(n, 12, replace=False).tolist() for _ in range(nv)]
     vdel = np.arange(0, 60, dtype=np.int32)
     def ins_vertices(g):
         first, applied = g.insert_vertices(vnb)
@@ -81,7 +82,7 @@ def test_allocation_failure_leaves_the_graph_unchanged(cm):
 
     def ins_vertices_ref(r):
         r.insert_vertices(vnb)
-        return 300 * 12          # every edge of a new vertex is new
+        return nv * 12           # every edge of a new vertex is new
 
     # (name, call, oracle call, allocations the call makes at least): the
     # insert grows the batch buffers, the edge index, the adjacency pool and
