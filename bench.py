@@ -253,10 +253,11 @@ def sweep_cases(batches):
 
 
 def sweep_config(args, n, m, sizes, ops):
+    laws = [nm for _, nm in SWEEP_LAWS if nm.split("-")[0] in args.laws.split(",")]
     c = {"workload": f"rmat{args.scale}-sweep", "scale": args.scale, "edge_factor": 16,
          "rmat_abcd": [0.57, 0.19, 0.19, 0.05], "vertices": n, "initial_edges": m, "batch_sizes": list(sizes),
-         "operations": list(ops), "laws": [nm for _, nm in SWEEP_LAWS],
-         "cases_per_step": len(sizes) * len(ops) * len(SWEEP_LAWS),
+         "operations": list(ops), "laws": laws,
+         "cases_per_step": len(sizes) * len(ops) * len(laws),
          "step": "every case once: its batch applied by one maintenance call, then undone untimed",
          "l2": "flushed before every timed call (256 MiB write)", "parallelism": "replicas"}
     if handle_options(args):
@@ -269,7 +270,8 @@ def sweep_inputs(args):
     sizes = tuple(int(x) for x in args.sizes.split(","))
     ops = tuple(args.ops.split(","))
     t0 = time.time()
-    n, e, batches = workloads.rmat_sweep(scale=args.scale, sizes=sizes, ops=ops)
+    laws = tuple(law for law, nm in SWEEP_LAWS if nm.split("-")[0] in args.laws.split(","))
+    n, e, batches = workloads.rmat_sweep(scale=args.scale, sizes=sizes, ops=ops, laws=laws)
     return n, e, batches, sizes, ops, time.time() - t0
 
 
@@ -286,6 +288,8 @@ def o3_law_rates(og, batches, sizes, ops, budget_s, offsets=None):
     out = {}
     for op in ops:
         for law, _ in SWEEP_LAWS:
+            if (op, max(sizes), law) not in batches:
+                continue
             b = batches[(op, max(sizes), law)]
             start = 0 if offsets is None else offsets.get((op, law), 0) % len(b)
             fwd = og.insert_edges if op == "insert" else og.delete_edges
@@ -308,6 +312,8 @@ def o3_estimate(rates, batches, sizes, ops):
     edges = t = 0.0
     for op in ops:
         for law, _ in SWEEP_LAWS:
+            if (op, law) not in rates:
+                continue
             done, secs = rates[(op, law)]
             for sz in sizes:
                 k = len(batches[(op, sz, law)])
@@ -1012,6 +1018,7 @@ def main():
     ap.add_argument("--scale", type=int, default=None)
     ap.add_argument("--sizes", default="1000,10000,100000,1000000")
     ap.add_argument("--ops", default="insert,delete")
+    ap.add_argument("--laws", default="uniform,degree", help="sweep endpoint laws: uniform, degree")
     ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", dest="ref_budget", type=float, default=4.0,
                     help="reference arm: seconds of O3 sampling per step")
