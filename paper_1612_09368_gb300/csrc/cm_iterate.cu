@@ -822,19 +822,36 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     if (MODE == 1) loop_control(P, C);   // thread 0 is the leader: its writes above come first
 }
 
+// Dynamic shared memory of both modes: one gather stage per warp.
+constexpr int kDynSmem = kGridWarps * kStageBytes;
+static_assert(kBlockThreads == kGridThreads, "both modes stage gathers for the same number of warps");
+
+// Lets both kernels take kDynSmem bytes of dynamic shared memory (host side,
+// once per process and device; harmless to repeat).
+static cudaError_t allow_dyn_smem() {
+    cudaError_t e = cudaFuncSetAttribute(maintain_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(maintain_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    return e;
+}
+
 int maintain_blocks_per_sm(int threads) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, maintain_kernel<0>, threads, 0) != cudaSuccess) return 0;
+    if (allow_dyn_smem() != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, maintain_kernel<0>, threads, kDynSmem) != cudaSuccess)
+        return 0;
     return nb;
 }
 
 // Cooperative (co-resident blocks, which the grid barrier needs); the
 // attribute form also records into a graph under stream capture.
 cudaError_t launch_maintain(const MaintainParams& p, int blocks, int threads, cudaStream_t s) {
+    cudaError_t e = allow_dyn_smem();
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kDynSmem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -850,7 +867,9 @@ const void* maintain_kernel_symbol(int mode) {
 
 cudaError_t launch_maintain_block(const MaintainParams& p, int threads, cudaStream_t s) {
     (void)threads;
-    maintain_kernel<1><<<1, kBlockThreads, 0, s>>>(p);
+    cudaError_t e = allow_dyn_smem();
+    if (e != cudaSuccess) return e;
+    maintain_kernel<1><<<1, kBlockThreads, kDynSmem, s>>>(p);
     return cudaGetLastError();
 }
 
