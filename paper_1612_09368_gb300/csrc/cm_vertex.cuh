@@ -107,6 +107,58 @@ __device__ __forceinline__ bool visit(const DevGraph& g, Ctl* C, int v, uint32_t
     return visit(g, C, v, e, vload64(iter_word(g, v)));
 }
 
+// The same two operations for the four slots of a lane's scan step, with
+// the four first atomics issued before any result is used (one round trip
+// per step instead of one per slot); a slot whose word changed since it was
+// gathered takes the slow path of add_word / visit.  Slots with want[q]
+// false are left alone.
+__device__ __forceinline__ void add_word4(const DevGraph& g, Ctl* C, const int (&v)[4], const bool (&want)[4],
+                                          uint32_t e, int32_t delta, const unsigned long long (&seen)[4],
+                                          uint32_t (&oflags)[4], int32_t (&ocount)[4]) {
+    const unsigned long long inc = (unsigned long long)(uint32_t)delta << 32;
+    const unsigned long long fresh = inc | (unsigned long long)(e << 2);
+    unsigned long long r[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        r[q] = 0;
+        if (want[q]) r[q] = same_iter(wz(seen[q]), e) ? atomicAdd(iter_word(g, v[q]), inc)
+                                                       : atomicCAS(iter_word(g, v[q]), seen[q], fresh);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        oflags[q] = 0;
+        ocount[q] = 0;
+        if (!want[q]) continue;
+        if (same_iter(wz(seen[q]), e)) {
+            oflags[q] = wz(r[q]) & 3u;
+            ocount[q] = ww(r[q]);
+        } else if (r[q] != seen[q]) {   // someone touched it first: restamp if needed, then add
+            make_current(g, C, v[q], e, r[q]);
+            const unsigned long long old = atomicAdd(iter_word(g, v[q]), inc);
+            oflags[q] = wz(old) & 3u;
+            ocount[q] = ww(old);
+        }
+    }
+}
+
+__device__ __forceinline__ void visit4(const DevGraph& g, Ctl* C, const int (&v)[4], bool (&cand)[4], uint32_t e,
+                                       const unsigned long long (&seen)[4]) {
+    const unsigned long long fresh = (unsigned long long)((e << 2) | kVisited);
+    unsigned long long r[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        r[q] = 0;
+        if (cand[q]) r[q] = same_iter(wz(seen[q]), e) ? atomicOr(iter_word(g, v[q]), (unsigned long long)kVisited)
+                                                       : atomicCAS(iter_word(g, v[q]), seen[q], fresh);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (!cand[q]) continue;
+        if (same_iter(wz(seen[q]), e)) cand[q] = (wz(r[q]) & kVisited) == 0;
+        else if (r[q] != seen[q]) cand[q] = visit(g, C, v[q], e, r[q]);
+    }
+}
+
 // ---------------------------------------------------------------- thread groups
 // A group of threads sharing one vertex's adjacency: one warp, or the block.
 struct WarpGroup {
@@ -383,11 +435,14 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
     scan_staged<Grp, false>(g, o, s0, s1, [&](const int (&w)[4], const int4 (&h)[4], const uint32_t (&c)[4],
                                               bool last) {
         bool p[4];
+        unsigned long long sw[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
-            p[q] = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
+            const bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
+            p[q] = h[q].x == k && h[q].y > k && !seen;
+            sw[q] = word_of(h[q]);
         }
+        visit4(g, C, w, p, e, sw);
         push_vertex4<ASYNC>(C, P, p, w, 0, last);
     });
 }
@@ -400,18 +455,19 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
                                                 long long o, int s0, int s1, uint32_t e) {
     scan_staged<Grp, false>(g, o, s0, s1, [&](const int (&w)[4], const int4 (&h)[4], const uint32_t (&c)[4],
                                               bool last) {
-        bool p[4];
+        bool cand[4], p[4];
+        unsigned long long sw[4];
+        uint32_t of[4];
+        int32_t oc[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const bool gone = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kProcessed) && h[q].w <= k;
-            p[q] = false;
-            if (h[q].x == k && h[q].y > k && !gone) {
-                uint32_t of;
-                int32_t oc;
-                add_word(g, C, w[q], e, -1, 0u, of, oc, word_of(h[q]));
-                p[q] = (of & kProcessed) && oc == k + 1;
-            }
+            cand[q] = h[q].x == k && h[q].y > k && !gone;
+            sw[q] = word_of(h[q]);
         }
+        add_word4(g, C, w, cand, e, -1, sw, of, oc);
+#pragma unroll
+        for (int q = 0; q < 4; q++) p[q] = cand[q] && (of[q] & kProcessed) && oc[q] == k + 1;
         push_vertex4<ASYNC>(C, P, p, w, 1, last);
     });
 }
@@ -424,21 +480,24 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
                                                 long long o, int s0, int s1, uint32_t e) {
     scan_staged<Grp, true>(g, o, s0, s1, [&](const int (&w)[4], const int4 (&h)[4], const uint32_t (&c)[4],
                                              bool last) {
-        bool p[4];
+        bool cand[4], p[4];
+        unsigned long long sw[4];
+        uint32_t of[4];
+        int32_t oc[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int thr = h[q].y - k + 1;
             const bool gone = thr <= 0 || (same_iter((uint32_t)h[q].z, e) && h[q].w >= thr);
-            p[q] = false;
             // evicted vertices (chg == e) are skipped: their cores already
             // dropped, so one that fell from k+1 would pass for level k
-            if (h[q].x == k && !gone && c[q] != e) {
-                uint32_t of;
-                int32_t oc;
-                add_word(g, C, w[q], e, 1, 0u, of, oc, word_of(h[q]));
-                p[q] = oc + 1 == thr;
-                if (p[q]) g.chg[w[q]] = e;
-            }
+            cand[q] = h[q].x == k && !gone && c[q] != e;
+            sw[q] = word_of(h[q]);
+        }
+        add_word4(g, C, w, cand, e, 1, sw, of, oc);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            p[q] = cand[q] && oc[q] + 1 == h[q].y - k + 1;
+            if (p[q]) g.chg[w[q]] = e;
         }
         push_vertex4<ASYNC>(C, P, p, w, 1, last);
     });
@@ -493,11 +552,14 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
             sup = __shfl_sync(0xffffffffu, sup, 0);
             if (sup > k) {
                 bool p[4];
+                unsigned long long sw[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
-                    p[q] = h[q].x == k && h[q].y > k && !seen && visit(g, C, w[q], e, word_of(h[q]));
+                    p[q] = h[q].x == k && h[q].y > k && !seen;
+                    sw[q] = word_of(h[q]);
                 }
+                visit4(g, C, w, p, e, sw);
                 push_vertex4<ASYNC>(C, P, p, w, 0, true);
             } else {
                 push_vertex<ASYNC>(C, P, lane == 0, v, 1, true);
