@@ -474,7 +474,7 @@ __device__ __forceinline__ void loop_control(const MaintainParams& P, Ctl* C) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE == 0 ? 2 : 1)
+__global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE == 0 ? 3 : 1)
     maintain_kernel(MaintainParams P) {
     Ctl* C = P.ctl;
     const DevGraph g = P.g;

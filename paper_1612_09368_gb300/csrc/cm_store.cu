@@ -172,15 +172,6 @@ cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, cudaStream_t s) {
 // warp takes after a barrier, so one high-degree vertex does not hold a whole
 // sub-wave on a single warp.
 //
-// A vertex that a warp's decrements bring to k goes to that warp's own
-// stack (kPeelStack entries in shared memory) and the warp peels it next,
-// depth first, without waiting for the next sub-wave's barrier; only what
-// overflows the stack goes to the frontier ring for the next sub-wave.  A
-// chain of departures then costs no barrier per link, and a wide burst
-// (more than the stack holds) still spreads over all warps.  The order in
-// which a level's departures are processed does not change which vertices
-// leave at that level.
-//
 // No counter is shared by the whole grid per vertex: the level scan
 // compacts a tile of kScanTile entries per block in shared memory and
 // appends it with one atomic per list; frontier vertices and chunk tasks
@@ -197,13 +188,11 @@ constexpr unsigned long long kPeelNoTask = ~0ull;
 constexpr int kScanTile = 4 * kPeelThreads;   // list entries per block and scan step
 constexpr int kPushBuf = 256;                 // per-warp buffer of peeled vertices
 constexpr int kPushFlush = kPushBuf - 128;    // a scan step adds at most 128
-constexpr int kPeelStack = 64;                // per-warp stack of departures peeled next
 
 struct PeelShared {
     int32_t keep[kScanTile];            // level scan: survivors of the tile
     int32_t peel[kScanTile];            // level scan: vertices of degree k
-    int32_t buf[kPeelWarps][kPushBuf];  // sub-waves: peeled vertices per warp (next sub-wave)
-    int32_t stk[kPeelWarps][kPeelStack];   // sub-waves: departures the warp peels itself
+    int32_t buf[kPeelWarps][kPushBuf];  // sub-waves: peeled vertices per warp
     int wcnt[kPeelWarps];
     int nkeep, npeel, mx;
     unsigned long long kbase, pbase, wbase;
@@ -240,12 +229,11 @@ __device__ __forceinline__ void block_flush_peeled(Ctl* C, const PeelParams& P, 
 
 // Slots [s0, s1) of the list at offset o (s0 a multiple of 4) at level k:
 // one degree off every neighbour; a neighbour that reaches k leaves now and
-// goes to the warp's stack, or, when the stack is full, to its buffer for
-// the next sub-wave.  Four slots per lane per step with one 16-byte load
-// (lists start 16-byte aligned, capacities are multiples of 4).
+// goes to the warp's buffer.  Four slots per lane per step with one 16-byte
+// load (lists start 16-byte aligned, capacities are multiples of 4).
 // Warp-collective.
 __device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& P, Ctl* C, long long o, int s0,
-                                           int s1, int k, int32_t* buf, int& cnt, int32_t* stk, int& nstk) {
+                                           int s1, int k, int32_t* buf, int& cnt) {
     const int lane = lane_id();
     for (int base = s0; base < s1; base += 128) {
         const int t0 = base + lane * 4;
@@ -265,57 +253,18 @@ __device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& 
             const int t = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += t;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int room = kPeelStack - nstk;
-        int at = incl - mine;   // rank of this lane's first departure in the step
+        int at = cnt + incl - mine;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (w[q] >= 0 && r[q] == k + 1) {
                 g.hs[w[q]].x = k;
-                if (at < room) stk[nstk + at] = w[q];
-                else buf[cnt + at - room] = w[q];
-                at++;
+                buf[at++] = w[q];
             }
         }
-        const int to_stack = total < room ? total : room;
-        nstk += to_stack;
-        cnt += total - to_stack;
+        cnt += __shfl_sync(0xffffffffu, incl, 31);
         __syncwarp();
         if (cnt > kPushFlush) flush_peeled(C, P, buf, cnt);
     }
-}
-
-// One departure at level k: its list is scanned by the warp, or cut into
-// chunk tasks for all warps when it has at least kPeelBig slots.  While the
-// chunk tasks of a sub-wave run (chunks false) the chunk list is being read,
-// so a high-degree departure goes to the next sub-wave instead.
-// Warp-collective.
-__device__ __forceinline__ void peel_vertex(const DevGraph& g, const PeelParams& P, Ctl* C, int v, int k, int32_t* buf,
-                                            int& cnt, int32_t* stk, int& nstk, long long& slots, bool chunks) {
-    const int lane = lane_id();
-    const long long o = g.off[v];
-    const int len = g.end[v];
-    if (len >= kPeelBig && !chunks) {
-        if (lane == 0) buf[cnt] = v;
-        cnt++;
-        __syncwarp();
-        if (cnt > kPushFlush) flush_peeled(C, P, buf, cnt);
-        return;
-    }
-    slots += len;
-    if (len >= kPeelBig) {
-        const int nch = (len + kPeelChunk - 1) / kPeelChunk;
-        unsigned long long tb = 0;
-        if (lane == 0) tb = atomicAdd(&C->pc[3], (unsigned long long)nch);
-        tb = __shfl_sync(0xffffffffu, tb, 0);
-        const bool fits = tb + nch <= P.chunk_cap;
-        for (int c = lane; c < nch; c += 32) {
-            if (tb + c >= P.chunk_cap) break;
-            P.chunks[tb + c] = fits ? (((unsigned long long)(uint32_t)v << 32) | (uint32_t)c) : kPeelNoTask;
-        }
-        if (fits) return;
-    }
-    peel_range(g, P, C, o, 0, len, k, buf, cnt, stk, nstk);
 }
 
 __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
@@ -329,8 +278,6 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
     const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
     int32_t* buf = S.buf[wib];
     int cnt = 0;
-    int32_t* stk = S.stk[wib];
-    int nstk = 0;
     bool ok;
     // live vertices start unpeeled with their live degree (compacted into
     // the remaining list a tile at a time, like the level scans below)
@@ -444,12 +391,25 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
         while (hi > lo) {
             const unsigned long long cnt_f = hi - lo;
             for (unsigned long long j = (unsigned long long)gwarp; j < cnt_f; j += (unsigned long long)nwarps) {
-                peel_vertex(g, P, C, P.F[lo + j], k, buf, cnt, stk, nstk, slots, true);
-                while (nstk > 0) {   // the departures this warp caused, depth first
-                    const int v = stk[--nstk];
-                    __syncwarp();
-                    peel_vertex(g, P, C, v, k, buf, cnt, stk, nstk, slots, true);
+                const int v = P.F[lo + j];
+                const long long o = g.off[v];
+                const int len = g.end[v];
+                slots += len;
+                if (len >= kPeelBig) {
+                    // chunk tasks (vertex, chunk), run by every warp after the barrier
+                    const int nch = (len + kPeelChunk - 1) / kPeelChunk;
+                    unsigned long long tb = 0;
+                    if (lane == 0) tb = atomicAdd(&C->pc[3], (unsigned long long)nch);
+                    tb = __shfl_sync(0xffffffffu, tb, 0);
+                    const bool fits = tb + nch <= P.chunk_cap;
+                    for (int c = lane; c < nch; c += 32) {
+                        if (tb + c >= P.chunk_cap) break;
+                        P.chunks[tb + c] = fits ? (((unsigned long long)(uint32_t)v << 32) | (uint32_t)c)
+                                                : kPeelNoTask;
+                    }
+                    if (fits) continue;
                 }
+                peel_range(g, P, C, o, 0, len, k, buf, cnt);
             }
             block_flush_peeled(C, P, S, cnt);
             if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
@@ -460,12 +420,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
                     if (task == kPeelNoTask) continue;
                     const int v = (int)(task >> 32);
                     const int s0 = (int)(task & 0xFFFFFFFFu) * kPeelChunk;
-                    peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k, buf, cnt, stk, nstk);
-                    while (nstk > 0) {
-                        const int u = stk[--nstk];
-                        __syncwarp();
-                        peel_vertex(g, P, C, u, k, buf, cnt, stk, nstk, slots, false);
-                    }
+                    peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k, buf, cnt);
                 }
                 block_flush_peeled(C, P, S, cnt);
                 if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
