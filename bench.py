@@ -133,6 +133,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
+def nvtx(push: bool):
+    """Brackets a measured maintenance call with an NVTX range named
+    "maintenance call" (a no-op unless a profiler listens)."""
+    try:
+        import torch
+        if push:
+            torch.cuda.nvtx.range_push("maintenance call")
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -357,7 +370,9 @@ def run_sweep(args):
             flush.fill_(j)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
+            nvtx(True)      # a profiler can keep the launches of the measured calls apart
             applied = fwd(inputs[j])
+            nvtx(False)
             a1.record(stream)
             a1.synchronize()
             st = g.stats()

@@ -436,8 +436,8 @@ static int build_store(cm_graph* h, const int32_t* dE, long long m, const int32_
         } else {
             if ((rc = peel_all(h))) break;
         }
-        h->launches++;
-        if ((e = init_mcd(g, 0, g.n, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "init_mcd"); break; }
+        h->launches += 2;
+        if ((e = init_mcd(g, 0, g.n, h->CQ, h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "init_mcd"); break; }
         if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = fail_cuda(h, e, "create"); break; }
     } while (0);
     cudaStreamSynchronize(h->stream);
@@ -616,7 +616,8 @@ extern "C" int cm_recompute_cores(cm_graph* h) {
     if ((rc = peel_all(h))) return end_call(h, rc);
     DevGraph g = h->g;
     g.n = h->n;
-    LAUNCH(h, init_mcd(g, 0, h->n, h->stream));
+    h->launches++;   // init_mcd launches two kernels
+    LAUNCH(h, init_mcd(g, 0, h->n, h->CQ, h->stream));   // CQ holds >= n entries
     CK(h, cudaEventRecord(h->ev[3], h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     float ms = 0;
@@ -696,19 +697,31 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
     g.n = h->n;
     int rc;
     if (op == CM_OP_INSERT && (rc = ensure_index(h, k))) return rc;
+    // A plain delete needs nothing from ingest on the host before the
+    // maintenance launches (no relocation, no index growth): the kept count
+    // stays on the device, the first launch takes it from there, and an
+    // invalid id stops every kernel after ingest (they test the error word
+    // first) before anything changed.  The host reads the control block
+    // once, at the end.
+    const bool device_count = op == CM_OP_DELETE && mode == 0 && !per_graph;
+    if (device_count && (rc = ensure_tasks(h))) return rc;
     CK(h, cudaMemsetAsync(h->bset, 0xFF, h->bset_size * sizeof(BSet), h->stream));
-    if ((rc = reset_ingest_zone(h))) return rc;
+    LAUNCH(h, ctl_reset_ingest(h->ctl, h->stream));
     LAUNCH(h, ingest_a(dE, k, nullptr, g, h->bset, h->bset_size - 1, h->ctl, h->stream));
     LAUNCH(h, ingest_b(dE, k, nullptr, op, g, h->bset, h->bset_size - 1, h->R0, h->OVL, h->ctl, h->stream));
-    if ((rc = rd_ctl(h))) return rc;
     Ctl& c = *h->hctl;
-    if (c.error == E_INVALID)
-        return set_err(h, CM_ERR_INVALID, "edge %lld of the batch names a vertex out of range or deleted", c.bad_index);
-    if (c.error) {
-        h->poisoned = true;
-        return set_err(h, CM_ERR_CUDA, "device error %d during ingest", c.error);
+    long long nrem0 = k;   // an upper bound until the count is read
+    if (!device_count) {
+        if ((rc = rd_ctl(h))) return rc;
+        if (c.error == E_INVALID)
+            return set_err(h, CM_ERR_INVALID, "edge %lld of the batch names a vertex out of range or deleted",
+                           c.bad_index);
+        if (c.error) {
+            h->poisoned = true;
+            return set_err(h, CM_ERR_CUDA, "device error %d during ingest", c.error);
+        }
+        nrem0 = (long long)c.nrem;
     }
-    const long long nrem0 = (long long)c.nrem;
     if (per_graph && h->dpergraph) {
         CK(h, cudaMemsetAsync(h->dpergraph, 0, (size_t)h->ngraphs * 8, h->stream));
         LAUNCH(h, count_multi(h->R0, nrem0, nullptr, h->dbases, h->ngraphs, h->dpergraph, h->stream));
@@ -756,7 +769,6 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
             CK(h, cudaMemset2DAsync((char*)g.hs + 8, sizeof(int4), 0, 8, (size_t)h->n, h->stream));
             h->epoch = 1;
         }
-        if ((rc = reset_launch_zone(h))) return rc;
         MaintainParams p = handle_params(h, op);
         p.max_iters = nrem0 + 1;
         int blocks, threads;
@@ -779,7 +791,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         }
         // where the call starts: all kept edges remain, in R0
         Resume rs{};
-        rs.nrem = (unsigned long long)nrem0;
+        rs.nrem = (unsigned long long)nrem0;   // replaced on the device by ingest's count (device_count)
         rs.rsel = 0;
         rs.epoch = h->epoch;
         rs.done = 0;
@@ -787,8 +799,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         // whole dense shell; the kernel hands down after a small iteration
         rs.want = 0;
         rs.iters = 0;
-        h->hctl->rs = rs;
-        CK(h, cudaMemcpyAsync(&h->ctl->rs, &h->hctl->rs, sizeof(Resume), cudaMemcpyHostToDevice, h->stream));
+        LAUNCH(h, ctl_begin_maintain(h->ctl, rs, device_count ? 1 : 0, h->stream));
         CK(h, cudaEventRecord(h->ev[2], h->stream));
         // grid launch then block launch: whichever the resume state names runs,
         // the other returns at once; a handover inside the pair needs no host.
@@ -805,6 +816,12 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
             want_grid = c.rs.want == 0;
         }
         CK(h, cudaEventRecord(h->ev[3], h->stream));
+        if (device_count) {   // what ingest found, read with the maintenance counters
+            if (c.error == E_INVALID)
+                return set_err(h, CM_ERR_INVALID, "edge %lld of the batch names a vertex out of range or deleted",
+                               c.bad_index);
+            nrem0 = (long long)c.nrem;
+        }
         if (c.error) {
             h->poisoned = true;
             const char* why = c.error == E_BARRIER_TIMEOUT ? "a grid barrier or task-queue wait ran out"

@@ -474,7 +474,7 @@ __device__ __forceinline__ void loop_control(const MaintainParams& P, Ctl* C) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE == 0 ? 3 : 1)
+__global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE == 0 ? 2 : 1)
     maintain_kernel(MaintainParams P) {
     Ctl* C = P.ctl;
     const DevGraph g = P.g;
@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     bool fx = false;
     unsigned long long fx_lo = 0, fx_hi = 0;
     uint32_t fx_e = 0;
-    int next_want = MODE, finished = 0;
+    // a call whose ingest kept no edge (its count read on the device) is done at once
+    int next_want = MODE, finished = (!mid && nrem == 0) ? 1 : 0;
     const int32_t* FXQ = P.op == 0 ? P.CQ : P.EQ;
     auto fixup_body = [&](int v, auto grp) { fixup_vertex<decltype(grp)>(g, v, fx_e, P.op, ls); };
 
@@ -822,36 +823,19 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
     if (MODE == 1) loop_control(P, C);   // thread 0 is the leader: its writes above come first
 }
 
-// Dynamic shared memory of both modes: one gather stage per warp.
-constexpr int kDynSmem = kGridWarps * kStageBytes;
-static_assert(kBlockThreads == kGridThreads, "both modes stage gathers for the same number of warps");
-
-// Lets both kernels take kDynSmem bytes of dynamic shared memory (host side,
-// once per process and device; harmless to repeat).
-static cudaError_t allow_dyn_smem() {
-    cudaError_t e = cudaFuncSetAttribute(maintain_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(maintain_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
-    return e;
-}
-
 int maintain_blocks_per_sm(int threads) {
     int nb = 0;
-    if (allow_dyn_smem() != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, maintain_kernel<0>, threads, kDynSmem) != cudaSuccess)
-        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, maintain_kernel<0>, threads, 0) != cudaSuccess) return 0;
     return nb;
 }
 
 // Cooperative (co-resident blocks, which the grid barrier needs); the
 // attribute form also records into a graph under stream capture.
 cudaError_t launch_maintain(const MaintainParams& p, int blocks, int threads, cudaStream_t s) {
-    cudaError_t e = allow_dyn_smem();
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = kDynSmem;
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -867,9 +851,7 @@ const void* maintain_kernel_symbol(int mode) {
 
 cudaError_t launch_maintain_block(const MaintainParams& p, int threads, cudaStream_t s) {
     (void)threads;
-    cudaError_t e = allow_dyn_smem();
-    if (e != cudaSuccess) return e;
-    maintain_kernel<1><<<1, kBlockThreads, kDynSmem, s>>>(p);
+    maintain_kernel<1><<<1, kBlockThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

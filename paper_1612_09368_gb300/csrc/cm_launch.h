@@ -63,6 +63,8 @@ struct PeelParams {
 };
 
 // ---- maintenance (cm_maintain.cu); kp / np: device item counts of a captured step (else NULL)
+cudaError_t ctl_reset_ingest(Ctl* c, cudaStream_t s);
+cudaError_t ctl_begin_maintain(Ctl* c, const Resume& rs, int take_nrem, cudaStream_t s);
 cudaError_t ingest_a(const int32_t* E, long long k, const unsigned long long* kp, DevGraph g, BSet* bs,
                      unsigned long long bmask, Ctl* c, cudaStream_t s);
 cudaError_t ingest_b(const int32_t* E, long long k, const unsigned long long* kp, int op, DevGraph g,
@@ -92,7 +94,8 @@ cudaError_t count_degrees(const int32_t* E, const uint32_t* ebkt, long long m, D
 cudaError_t assign_offsets(DevGraph g, int32_t v0, int32_t v1, Ctl* c, cudaStream_t s);
 cudaError_t scatter_edges(const int32_t* E, const uint32_t* ebkt, long long m, DevGraph g, cudaStream_t s);
 cudaError_t set_cores(const int32_t* cores, DevGraph g, cudaStream_t s);
-cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, cudaStream_t s);
+// core_scratch: n int32 of scratch (receives a compact copy of the cores)
+cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, int32_t* core_scratch, cudaStream_t s);
 cudaError_t launch_peel(const PeelParams& p, int blocks, int threads, cudaStream_t s);
 int peel_blocks_per_sm(int threads);
 cudaError_t rehash(const Bucket* old_idx, unsigned long long old_size, DevGraph g, Ctl* c, cudaStream_t s);

@@ -2,6 +2,7 @@
 // batch and the edge index), relocation of vertices whose slack a batch
 // exceeds, and the structure-only apply used by the re-peel comparator.
 // The superior-edge-set iterations themselves are in cm_iterate.cu.
+#include <cstddef>
 #include <cstdio>
 
 #include "cm_common.cuh"
@@ -15,6 +16,48 @@ namespace cm {
 // skips its remaining kernels once Ctl::defer is set.
 __device__ __forceinline__ long long item_count(long long k, const unsigned long long* kp) {
     return kp ? (long long)vload64(kp) : k;
+}
+
+// ------------------------------------------------------------------ control block
+// One launch instead of a row of small memsets and copies before a call's
+// kernels: the host-exchange words ingest fills (error, kept and overflow
+// counts, smallest bad position), and, before the maintenance launches, the
+// barrier words, ring tails, counters and timers, plus the resume record
+// the first launch reads.  take_nrem: the remaining-edge count is the one
+// ingest left in the control block (the host did not read it back).
+__global__ void ctl_reset_ingest_kernel(Ctl* c) {
+    c->error = 0;
+    c->err_info = 0;
+    c->nrem = 0;
+    c->noverflow = 0;
+    c->reloc_need = 0;
+    c->bad_index = 0x7F7F7F7F7F7F7F7FLL;   // larger than any position
+    c->gather_n = 0;
+    c->defer = 0;
+}
+
+__global__ void ctl_begin_maintain_kernel(Ctl* c, Resume rs, int take_nrem) {
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(c);
+    constexpr int head = (int)(offsetof(Ctl, error) / 8);
+    constexpr int z0 = (int)(offsetof(Ctl, tail) / 8), z1 = (int)(offsetof(Ctl, nrem) / 8);
+    static_assert(offsetof(Ctl, error) % 8 == 0 && offsetof(Ctl, tail) % 8 == 0 && offsetof(Ctl, nrem) % 8 == 0,
+                  "zeroed ranges are whole 8-byte words");
+    for (int i = threadIdx.x; i < head; i += blockDim.x) w[i] = 0;
+    for (int i = z0 + threadIdx.x; i < z1; i += blockDim.x) w[i] = 0;
+    if (threadIdx.x == 0) {
+        if (take_nrem) rs.nrem = c->nrem;
+        c->rs = rs;
+    }
+}
+
+cudaError_t ctl_reset_ingest(Ctl* c, cudaStream_t s) {
+    ctl_reset_ingest_kernel<<<1, 1, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t ctl_begin_maintain(Ctl* c, const Resume& rs, int take_nrem, cudaStream_t s) {
+    ctl_begin_maintain_kernel<<<1, 256, 0, s>>>(c, rs, take_nrem);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ ingest

@@ -98,13 +98,21 @@ __global__ void set_cores_kernel(const int32_t* __restrict__ cores, DevGraph g) 
 // SD(v), Definition 7: neighbours with core >= core(v).  Warp per vertex;
 // four slots per lane per step with one 16-byte list load (lists start
 // 16-byte aligned and their capacity is a multiple of 4) and the four
-// neighbour gathers issued before any is used.
-__global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1) {
+// neighbour gathers issued before any is used.  The cores are read from a
+// compact copy (4 bytes per vertex, which stays in L2 at the sizes here)
+// instead of the 16-byte vertex words.
+__global__ void copy_cores_kernel(DevGraph g, int32_t* core) {
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n) return;
+    core[v] = g.hs[v].x;
+}
+
+__global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1, const int32_t* __restrict__ core) {
     long long w = v0 + (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     int lane = lane_id();
     for (; w < v1; w += nw) {
-        int k = g.hs[w].x;
+        int k = core[w];
         if (k < 0) continue;
         long long o = g.off[w];
         int len = g.end[w], sd = 0;
@@ -113,7 +121,7 @@ __global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1) {
             const int x[4] = {a.x, t0 + 1 < len ? a.y : HOLE, t0 + 2 < len ? a.z : HOLE, t0 + 3 < len ? a.w : HOLE};
             int c[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) c[q] = x[q] >= 0 ? g.hs[x[q]].x : -1;
+            for (int q = 0; q < 4; q++) c[q] = x[q] >= 0 ? core[x[q]] : -1;
 #pragma unroll
             for (int q = 0; q < 4; q++) sd += c[q] >= k;
         }
@@ -147,9 +155,10 @@ cudaError_t set_cores(const int32_t* cores, DevGraph g, cudaStream_t s) {
     set_cores_kernel<<<grid_for(g.n, 256, 1ll << 31), 256, 0, s>>>(cores, g);
     return cudaGetLastError();
 }
-cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, cudaStream_t s) {
+cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, int32_t* core_scratch, cudaStream_t s) {
     if (v1 <= v0) return cudaSuccess;
-    init_mcd_kernel<<<grid_for((long long)(v1 - v0) * 32, 256, 65536), 256, 0, s>>>(g, v0, v1);
+    copy_cores_kernel<<<grid_for(g.n, 256, 1ll << 31), 256, 0, s>>>(g, core_scratch);
+    init_mcd_kernel<<<grid_for((long long)(v1 - v0) * 32, 256, 65536), 256, 0, s>>>(g, v0, v1, core_scratch);
     return cudaGetLastError();
 }
 

@@ -108,10 +108,9 @@ __device__ __forceinline__ bool visit(const DevGraph& g, Ctl* C, int v, uint32_t
 }
 
 // The same two operations for the four slots of a lane's scan step, with
-// the four first atomics issued before any result is used (one round trip
-// per step instead of one per slot); a slot whose word changed since it was
-// gathered takes the slow path of add_word / visit.  Slots with want[q]
-// false are left alone.
+// the four first atomics issued before any result is used; a slot whose
+// word changed since it was gathered takes the slow path of add_word /
+// visit.  Slots with want[q] / cand[q] false are left alone.
 __device__ __forceinline__ void add_word4(const DevGraph& g, Ctl* C, const int (&v)[4], const bool (&want)[4],
                                           uint32_t e, int32_t delta, const unsigned long long (&seen)[4],
                                           uint32_t (&oflags)[4], int32_t (&ocount)[4]) {
@@ -315,100 +314,32 @@ __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, i
 #define SCAN4_BEGIN(Grp, len) SCAN4_RANGE(Grp, 0, len)
 #define SCAN4_END }
 
-// ---------------------------------------------------------------- staged gathers
-// The range scans below stage the neighbours' 16-byte vertex words in
-// shared memory with cp.async, two steps deep: the gathers of step i+1 are
-// issued before the body of step i runs, so a step's atomics and queue
-// pushes overlap the next step's gathers instead of waiting in one chain
-// (list read -> gather -> atomic -> push) per step.  The copies land in a
-// per-warp area of the kernel's dynamic shared memory and take no registers
-// while in flight.  Vertex words are copied past L1 (.cg): they are read
-// once per slot and written by atomics at L2.  Deletion also needs the
-// neighbours' change stamps: they are loaded one step ahead into registers.
-struct WarpStage {
-    int4 h[2][32][4];       // vertex words of two steps, four slots per lane
-};
-constexpr int kStageBytes = (int)sizeof(WarpStage);
-extern __shared__ __align__(16) unsigned char g_dyn_smem[];
-__device__ __forceinline__ WarpStage& warp_stage() {
-    return reinterpret_cast<WarpStage*>(g_dyn_smem)[threadIdx.x >> 5];
-}
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// The list word of this lane for the step at slot t (4 slots, HOLE past s1).
-__device__ __forceinline__ int4 list_word(const DevGraph& g, long long o, int t, int s1) {
-    int4 a = make_int4(HOLE, HOLE, HOLE, HOLE);
-    if (t < s1) a = __ldcs(reinterpret_cast<const int4*>(g.adj + o + t));   // streamed: keep L2 for vertex words
-    if (t + 1 >= s1) a.y = HOLE;
-    if (t + 2 >= s1) a.z = HOLE;
-    if (t + 3 >= s1) a.w = HOLE;
-    return a;
-}
-
-// Issues the gathers of one step into stage `st` (a hole gets the word of
-// no vertex: core -1); with CHG, loads the step's change stamps into c.
-template <bool CHG>
-__device__ __forceinline__ void stage_step(const DevGraph& g, WarpStage& S, int st, const int4& a, uint32_t (&c)[4]) {
-    const int lane = lane_id();
-    const int w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        if (w[q] >= 0) cp_async16(&S.h[st][lane][q], &g.hs[w[q]]);
-        else S.h[st][lane][q] = make_int4(-1, 0, 0, 0);
+// The same walk with the list read two steps ahead: each lane loads the
+// 16-byte words of two consecutive steps before the first step's gathers,
+// so a step's neighbour gathers do not wait behind its own list read.  List
+// reads are streamed (evict-first) so that L2 keeps the vertex words.
+// Inside, `int w[4]` holds the step's four neighbour ids (HOLE past s1)
+// and `last_` is set in the group's last step.
+#define SCANP_RANGE(Grp, o, s0, s1)                                                              \
+    for (int blk_ = (s0) + Grp::first() * 4; blk_ < (s1); blk_ += Grp::G * 8) {                  \
+        int4 A_[2];                                                                               \
+        _Pragma("unroll") for (int j_ = 0; j_ < 2; j_++) {                                         \
+            const int t_ = blk_ + j_ * Grp::G * 4 + lane_id() * 4;                                \
+            A_[j_] = t_ < (s1) ? __ldcs(reinterpret_cast<const int4*>(g.adj + (o) + t_))                 \
+                               : make_int4(HOLE, HOLE, HOLE, HOLE);                               \
+        }                                                                                         \
+        _Pragma("unroll") for (int j_ = 0; j_ < 2; j_++) {                                         \
+            if (blk_ + j_ * Grp::G * 4 >= (s1)) break;                                            \
+            const int t0_ = blk_ + j_ * Grp::G * 4 + lane_id() * 4;                               \
+            const bool last_ = blk_ + (j_ + 1) * Grp::G * 4 >= (s1);                              \
+            int w[4];                                                                             \
+            w[0] = A_[j_].x;                                                                      \
+            w[1] = t0_ + 1 < (s1) ? A_[j_].y : HOLE;                                              \
+            w[2] = t0_ + 2 < (s1) ? A_[j_].z : HOLE;                                              \
+            w[3] = t0_ + 3 < (s1) ? A_[j_].w : HOLE;
+#define SCANP_END \
+        }         \
     }
-    if (CHG) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) c[q] = w[q] >= 0 ? g.chg[w[q]] : 0u;
-    }
-}
-
-// Walks slots [s0, s1) of the list at offset o (s0 a multiple of 4), four
-// slots per lane per step, and calls body(w, h, c, last) for every step of
-// this warp: w the four neighbour ids (HOLE past s1), h their vertex words,
-// c their change stamps (CHG only), last whether this is the group's last
-// step.  Steps are warp-uniform, so the body may use warp collectives.
-template <class Grp, bool CHG, class Body>
-__device__ __forceinline__ void scan_staged(const DevGraph& g, long long o, int s0, int s1, Body body) {
-    constexpr int STEP = Grp::G * 4;
-    const int lane = lane_id();
-    const int first = s0 + Grp::first() * 4;
-    if (first >= s1) return;
-    WarpStage& S = warp_stage();
-    int4 cur = list_word(g, o, first + lane * 4, s1);
-    int4 nxt = list_word(g, o, first + STEP + lane * 4, s1);
-    uint32_t c[4] = {0u, 0u, 0u, 0u}, cn[4] = {0u, 0u, 0u, 0u};
-    stage_step<CHG>(g, S, 0, cur, c);
-    cp_async_commit();
-    for (int i = 0, b = first; b < s1; i++, b += STEP) {
-        const bool more = b + STEP < s1;
-        if (more) stage_step<CHG>(g, S, (i + 1) & 1, nxt, cn);
-        cp_async_commit();
-        cp_async_wait<1>();   // this step's copies (all but the newest group) have landed
-        __syncwarp();
-        const int w[4] = {cur.x, cur.y, cur.z, cur.w};
-        int4 h[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) h[q] = S.h[i & 1][lane][q];
-        body(w, h, c, !more);
-        cur = nxt;
-        if (CHG) {
-#pragma unroll
-            for (int q = 0; q < 4; q++) c[q] = cn[q];
-        }
-        if (more) nxt = list_word(g, o, b + 2 * STEP + lane * 4, s1);
-        __syncwarp();   // every lane read stage i & 1 before it is refilled
-    }
-    cp_async_wait<0>();
-}
 
 // ---------------------------------------------------------------- range scans
 // Each scan covers slots [s0, s1) of the list at offset o of a vertex at
@@ -420,10 +351,13 @@ __device__ __forceinline__ void scan_staged(const DevGraph& g, long long o, int 
 template <class Grp>
 __device__ __forceinline__ int csd_part(const DevGraph& g, int k, long long o, int s0, int s1) {
     int pcd = 0;
-    scan_staged<Grp, false>(g, o, s0, s1, [&](const int (&w)[4], const int4 (&h)[4], const uint32_t (&c)[4], bool) {
+    SCANP_RANGE(Grp, o, s0, s1)
+        int2 h[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? *reinterpret_cast<const int2*>(&g.hs[w[q]]) : make_int2(-1, 0);
 #pragma unroll
         for (int q = 0; q < 4; q++) pcd += (h[q].x > k) || (h[q].x == k && h[q].y > k);
-    });
+    SCANP_END
     return pcd;
 }
 
@@ -432,8 +366,10 @@ __device__ __forceinline__ int csd_part(const DevGraph& g, int k, long long o, i
 template <class Grp, bool ASYNC>
 __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k, long long o,
                                              int s0, int s1, uint32_t e) {
-    scan_staged<Grp, false>(g, o, s0, s1, [&](const int (&w)[4], const int4 (&h)[4], const uint32_t (&c)[4],
-                                              bool last) {
+    SCANP_RANGE(Grp, o, s0, s1)
+        int4 h[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
         bool p[4];
         unsigned long long sw[4];
 #pragma unroll
@@ -443,8 +379,8 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
             sw[q] = word_of(h[q]);
         }
         visit4(g, C, w, p, e, sw);
-        push_vertex4<ASYNC>(C, P, p, w, 0, last);
-    });
+        push_vertex4<ASYNC>(C, P, p, w, 0, last_);
+    SCANP_END
 }
 
 // InsertRemove over the range (Algorithm 4): every core-k neighbour with
@@ -453,8 +389,10 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
 template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
                                                 long long o, int s0, int s1, uint32_t e) {
-    scan_staged<Grp, false>(g, o, s0, s1, [&](const int (&w)[4], const int4 (&h)[4], const uint32_t (&c)[4],
-                                              bool last) {
+    SCANP_RANGE(Grp, o, s0, s1)
+        int4 h[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
         bool cand[4], p[4];
         unsigned long long sw[4];
         uint32_t of[4];
@@ -468,8 +406,8 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
         add_word4(g, C, w, cand, e, -1, sw, of, oc);
 #pragma unroll
         for (int q = 0; q < 4; q++) p[q] = cand[q] && (of[q] & kProcessed) && oc[q] == k + 1;
-        push_vertex4<ASYNC>(C, P, p, w, 1, last);
-    });
+        push_vertex4<ASYNC>(C, P, p, w, 1, last_);
+    SCANP_END
 }
 
 // DeleteRemove over the range (Algorithm 7): each core-k neighbour w loses
@@ -478,8 +416,14 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
 template <class Grp, bool ASYNC>
 __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
                                                 long long o, int s0, int s1, uint32_t e) {
-    scan_staged<Grp, true>(g, o, s0, s1, [&](const int (&w)[4], const int4 (&h)[4], const uint32_t (&c)[4],
-                                             bool last) {
+    SCANP_RANGE(Grp, o, s0, s1)
+        int4 h[4];
+        uint32_t c[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+            c[q] = w[q] >= 0 ? g.chg[w[q]] : 0u;
+        }
         bool cand[4], p[4];
         unsigned long long sw[4];
         uint32_t of[4];
@@ -499,8 +443,8 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
             p[q] = cand[q] && oc[q] + 1 == h[q].y - k + 1;
             if (p[q]) g.chg[w[q]] = e;
         }
-        push_vertex4<ASYNC>(C, P, p, w, 1, last);
-    });
+        push_vertex4<ASYNC>(C, P, p, w, 1, last_);
+    SCANP_END
 }
 
 // ---------------------------------------------------------------- per-vertex phase bodies

@@ -310,6 +310,10 @@ def test_edge_cases(cm):
     with pytest.raises(cm.CoreMaintError) as ei:
         g.insert_edges(np.array([[3, 10]], np.int32))               # dead vertex
     assert ei.value.code == cm.CM_ERR_INVALID
+    with pytest.raises(cm.CoreMaintError) as ei:
+        g.delete_edges(np.array([[5, 6], [3, 4]], np.int32))        # a delete naming a dead vertex
+    assert ei.value.code == cm.CM_ERR_INVALID
+    assert g.m == m0 - 2                                            # vertex 3's two edges went, nothing else
     with pytest.raises(cm.CoreMaintError):
         g.delete_vertices(np.array([3], np.int32))                  # already dead
     with pytest.raises(cm.CoreMaintError):
