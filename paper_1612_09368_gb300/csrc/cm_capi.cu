@@ -186,14 +186,16 @@ static int grow_vertices(cm_graph* h, int32_t need) {
     int32_t keep = h->n;
     DevGraph& g = h->g;
     size_t oc = (size_t)h->ncap;
-    bool ok = realloc_dev(h, g.hs, oc, nc, keep) && realloc_dev(h, g.off, oc, nc, keep) &&
+    bool ok = realloc_dev(h, g.hc, oc, nc, keep) && realloc_dev(h, g.hw, oc, nc, keep) &&
+              realloc_dev(h, g.off, oc, nc, keep) &&
               realloc_dev(h, g.end, oc, nc, keep) && realloc_dev(h, g.cap, oc, nc, keep) &&
               realloc_dev(h, g.deg, oc, nc, keep) && realloc_dev(h, g.chg, oc, nc, keep) &&
               realloc_dev(h, g.taken, oc, nc, keep) && realloc_dev(h, g.claim0, oc, nc, keep) &&
               realloc_dev(h, g.claim1, oc, nc, keep) && realloc_dev(h, g.need, oc, nc, keep);
     if (!ok) return set_err(h, CM_ERR_OOM, "out of device memory growing vertex arrays to %lld", nc);
     size_t tail = (size_t)(nc - keep);
-    CK(h, cudaMemsetAsync(g.hs + keep, 0, tail * sizeof(int4), h->stream));
+    CK(h, cudaMemsetAsync(g.hc + keep, 0, tail * sizeof(int2), h->stream));
+    CK(h, cudaMemsetAsync(g.hw + keep, 0, tail * sizeof(unsigned long long), h->stream));
     CK(h, cudaMemsetAsync(g.end + keep, 0, tail * sizeof(int32_t), h->stream));
     CK(h, cudaMemsetAsync(g.cap + keep, 0, tail * sizeof(int32_t), h->stream));
     CK(h, cudaMemsetAsync(g.deg + keep, 0, tail * sizeof(int32_t), h->stream));
@@ -363,7 +365,8 @@ static void free_all(cm_graph* h) {
     cudaDeviceSynchronize();
     DevGraph& g = h->g;
     size_t nc = (size_t)h->ncap;
-    dfree(h, g.hs, nc * sizeof(int4));
+    dfree(h, g.hc, nc * sizeof(int2));
+    dfree(h, g.hw, nc * sizeof(unsigned long long));
     dfree(h, g.off, nc * 8);
     dfree(h, g.end, nc * 4);
     dfree(h, g.cap, nc * 4);
@@ -766,7 +769,7 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         if (h->epoch > 0x3F000000u) {   // 30-bit stamps about to wrap: clear them
             CK(h, cudaMemsetAsync(g.chg, 0, (size_t)h->n * 4, h->stream));
             CK(h, cudaMemsetAsync(g.taken, 0, (size_t)h->n * 4, h->stream));
-            CK(h, cudaMemset2DAsync((char*)g.hs + 8, sizeof(int4), 0, 8, (size_t)h->n, h->stream));
+            CK(h, cudaMemsetAsync(g.hw, 0, (size_t)h->n * sizeof(unsigned long long), h->stream));
             h->epoch = 1;
         }
         MaintainParams p = handle_params(h, op);
@@ -1584,7 +1587,7 @@ static int step_prepare(cm_step* s, long long kins) {
         DevGraph& g = h->g;
         CK(h, cudaMemsetAsync(g.chg, 0, (size_t)h->n * 4, h->stream));
         CK(h, cudaMemsetAsync(g.taken, 0, (size_t)h->n * 4, h->stream));
-        CK(h, cudaMemset2DAsync((char*)g.hs + 8, sizeof(int4), 0, 8, (size_t)h->n, h->stream));
+        CK(h, cudaMemsetAsync(g.hw, 0, (size_t)h->n * sizeof(unsigned long long), h->stream));
         h->epoch = 1;
     }
     *s->hEpoch = h->epoch;
@@ -1714,7 +1717,7 @@ extern "C" int cm_step_run(cm_step* s, const int64_t* ins_counts, const int32_t*
 // are restored, so each trial replays the same work from the same graph.
 struct Snapshot {
     size_t nv = 0, adj = 0, idx = 0;
-    int4* hs = nullptr;
+    unsigned char* words = nullptr;   // hc then hw (16 bytes per vertex)
     int64_t* off = nullptr;
     int32_t* i32 = nullptr;        // end, cap, deg, chg, taken (5 x nv)
     unsigned long long* claims = nullptr;   // claim0, claim1 (2 x nv)
@@ -1727,7 +1730,7 @@ struct Snapshot {
 };
 
 static void snap_free(cm_graph* h, Snapshot& z) {
-    dfree(h, z.hs, z.nv * sizeof(int4));
+    dfree(h, z.words, z.nv * 16);
     dfree(h, z.off, z.nv * 8);
     dfree(h, z.i32, z.nv * 4 * 5);
     dfree(h, z.claims, z.nv * 8 * 2);
@@ -1745,7 +1748,8 @@ static int snap_copy(cm_graph* h, Snapshot& z, bool save) {
         return save ? cudaMemcpyAsync(snap, live, bytes, kd, st) : cudaMemcpyAsync(live, snap, bytes, kd, st);
     };
     const size_t nv = z.nv;
-    CK(h, cp(z.hs, g.hs, nv * sizeof(int4)));
+    CK(h, cp(z.words, g.hc, nv * 8));
+    CK(h, cp(z.words + nv * 8, g.hw, nv * 8));
     CK(h, cp(z.off, g.off, nv * 8));
     CK(h, cp(z.i32 + 0 * nv, g.end, nv * 4));
     CK(h, cp(z.i32 + 1 * nv, g.cap, nv * 4));
@@ -1779,14 +1783,14 @@ static int snap_take(cm_graph* h, Snapshot& z) {
     z.nv = (size_t)h->n;
     z.adj = (size_t)h->hctl->adj_top;
     z.idx = (size_t)h->idx_size;
-    z.hs = (int4*)dalloc(h, z.nv * sizeof(int4));
+    z.words = (unsigned char*)dalloc(h, z.nv * 16);
     z.off = (int64_t*)dalloc(h, z.nv * 8);
     z.i32 = (int32_t*)dalloc(h, z.nv * 4 * 5);
     z.claims = (unsigned long long*)dalloc(h, z.nv * 8 * 2);
     z.pool = (int32_t*)dalloc(h, z.adj * 4);
     z.index = (Bucket*)dalloc(h, z.idx * sizeof(Bucket));
     z.ctl = (Ctl*)dalloc(h, sizeof(Ctl));
-    if (!z.hs || !z.off || !z.i32 || !z.claims || !z.pool || !z.index || !z.ctl) {
+    if (!z.words || !z.off || !z.i32 || !z.claims || !z.pool || !z.index || !z.ctl) {
         snap_free(h, z);
         return set_err(h, CM_ERR_OOM, "out of device memory for the tuner's copy of the graph");
     }

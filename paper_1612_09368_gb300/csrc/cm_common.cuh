@@ -1,12 +1,16 @@
 // cm_common.cuh -- device-side layout and primitives shared by the kernels.
 //
 // Device layout of one graph (all arrays indexed by vertex id unless noted):
-//   hs[v]   int4  {core, mcd, stamp, count}: the hot per-vertex word.  core is
-//           the core number (-1 dead); mcd is SD(v), the superior degree
-//           (Section IV, Definition 7: neighbours with core >= core(v));
-//           stamp/count are per-iteration scratch (insert: visit epoch and
-//           support count; delete: epoch and decrement count, updated as one
-//           64-bit word).  Packing them gives one 16-byte gather per neighbour.
+//   hc[v]   int2  {core, SD}: core is the core number (-1 dead); SD is the
+//           superior degree (Section IV, Definition 7: neighbours with core
+//           >= core(v)).  Every scan step gathers these 8 bytes per
+//           neighbour; at 2^24 vertices the array is half the size of a
+//           16-byte word per vertex, so twice as much of it stays in L2 and a
+//           32-byte sector carries four vertices instead of two.
+//   hw[v]   u64   the per-iteration word: low 32 bits a stamp (iteration << 2
+//           | flags), high 32 bits a count (insert: visited / processed
+//           flags and support; delete: evicted-neighbour count).  Scans load
+//           it only for the neighbours that can be candidates at their level.
 //   off[v]  int64 first adjacency slot; end[v] used slots (live + holes);
 //   cap[v]  allocated slots (multiple of 4, so lists start 16-byte aligned);
 //   deg[v]  live degree.  adj[] holds neighbour ids, HOLE (-1) for a deleted
@@ -85,7 +89,10 @@ constexpr int kTails = 4;
 // kind: HUB_FRONT (insert frontier: chunks sum CSD, the last one decides),
 // HUB_EVICT_INS / HUB_EVICT_DEL (eviction scans), HUB_EXPAND (visit the
 // frontier neighbours of a hub whose support stayed above k).
-enum { HUB_FRONT = 0, HUB_EVICT_INS = 1, HUB_EVICT_DEL = 2, HUB_EXPAND = 3 };
+// HUB_FRONT_SPEC: as HUB_FRONT, but each chunk also visits its candidates
+// at once (speculative expansion, see process_frontier), so no HUB_EXPAND
+// round follows.
+enum { HUB_FRONT = 0, HUB_EVICT_INS = 1, HUB_EVICT_DEL = 2, HUB_EXPAND = 3, HUB_FRONT_SPEC = 4 };
 struct __align__(16) HubItem {
     long long off;                 // adjacency offset
     int32_t v, kind, k, len;
@@ -152,7 +159,8 @@ struct DevGraph {
     int32_t slack_pct;
     int32_t min_cap;
     int32_t pad;
-    int4* hs;
+    int2* hc;
+    unsigned long long* hw;
     int64_t* off;
     int32_t* end;
     int32_t* cap;

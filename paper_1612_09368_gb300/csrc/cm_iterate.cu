@@ -223,8 +223,9 @@ __device__ __forceinline__ void run_chunk(const DevGraph& g, Ctl* C, const Maint
     const int len = vload32i(&it->len), nch = vload32i(&it->nch);
     const long long off = (long long)vload64((const unsigned long long*)&it->off);
     const int s0 = ci * kChunk, s1 = min(s0 + kChunk, len);
-    if (kind == HUB_FRONT) {
-        const int part = WG::sum(csd_part<WG>(g, k, off, s0, s1));
+    if (kind == HUB_FRONT || kind == HUB_FRONT_SPEC) {
+        const int part = WG::sum(kind == HUB_FRONT_SPEC ? csd_expand_range<WG, true>(g, C, P, k, off, s0, s1, e)
+                                                        : csd_part<WG>(g, k, off, s0, s1));
         int decide = 0;   // 1 expand, 2 evict
         if (lane == 0) {
             atomicAdd(&it->acc, part);
@@ -242,7 +243,7 @@ __device__ __forceinline__ void run_chunk(const DevGraph& g, Ctl* C, const Maint
             }
         }
         decide = __shfl_sync(0xffffffffu, decide, 0);
-        if (decide == 1 && !make_hub(C, P, v, HUB_EXPAND, k, off, len))
+        if (decide == 1 && kind == HUB_FRONT && !make_hub(C, P, v, HUB_EXPAND, k, off, len))
             expand_range<WG, true>(g, C, P, k, off, 0, len, e);
         if (decide == 2) push_vertex<true>(C, P, lane == 0, v, 1, true);
         return;
@@ -254,7 +255,7 @@ __device__ __forceinline__ void run_chunk(const DevGraph& g, Ctl* C, const Maint
     if (lane == 0) {
         __threadfence();
         if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
-            if (kind == HUB_EVICT_DEL) g.hs[v].x = k - 1;
+            if (kind == HUB_EVICT_DEL) g.hc[v].x = k - 1;
             if (kind != HUB_EXPAND) {
                 ls.ev++;
                 ls.evl += len;
@@ -359,7 +360,8 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
             const VInfo vi = load_vinfo(g, v);
             const bool hub = P.hub_len > 0 && vi.len >= P.hub_len;
             if (type == T_FRONT) {
-                if (!hub || !make_hub(C, P, v, HUB_FRONT, vi.h.x, vi.o, vi.len))
+                if (!hub || !make_hub(C, P, v, expand_early(vi.h.y, vi.h.x) ? HUB_FRONT_SPEC : HUB_FRONT, vi.h.x,
+                                      vi.o, vi.len))
                     process_frontier<WG, true>(g, C, P, v, vi, e, ls);
             } else if (P.op == 0) {
                 if (!hub || !make_hub(C, P, v, HUB_EVICT_INS, vi.h.x, vi.o, vi.len))
@@ -399,8 +401,8 @@ __device__ __forceinline__ void seed_tasks(Ctl* C, const MaintainParams& P, cons
 // An edge's core number k = min(core(lo), core(hi)) and its constrained
 // endpoints: those whose core is k (Definition 6), except pinned vertices.
 __device__ __forceinline__ void edge_level(const DevGraph& g, const REdge& E, int& k, bool& clo, bool& chi) {
-    const int2 a = *reinterpret_cast<const int2*>(&g.hs[E.lo]);
-    const int2 b = *reinterpret_cast<const int2*>(&g.hs[E.hi]);
+    const int2 a = g.hc[E.lo];
+    const int2 b = g.hc[E.hi];
     k = min(a.x, b.x);
     clo = a.x == k && a.y < PIN_SD;
     chi = b.x == k && b.y < PIN_SD;
@@ -413,13 +415,16 @@ __device__ __forceinline__ unsigned long long edge_prio(const REdge& E, bool by_
     return by_key ? key : fmix64(key);
 }
 
-// Selection, claim phase of round r.
+// Selection, claim phase of round r.  An edge already selected or blocked
+// that did not claim in round r-1 has nothing to do and gathers nothing.
 __device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e, bool by_key) {
     REdge E = R[i];
+    const uint32_t f = E.flags;
+    const bool claimed_last = r > 0 && (f >> 2) == (uint32_t)r;
+    if ((f & (F_SEL | F_BLK)) && !claimed_last) return;
     int k; bool clo, chi;
     edge_level(g, E, k, clo, chi);
-    uint32_t f = E.flags;
-    if (r > 0 && (f >> 2) == (uint32_t)r) {   // claimed in round r-1: clear that buffer
+    if (claimed_last) {   // claimed in round r-1: clear that buffer
         unsigned long long* cb = ((r - 1) & 1) ? g.claim1 : g.claim0;
         if (clo) cb[E.lo] = CLAIM_FREE;
         if (chi) cb[E.hi] = CLAIM_FREE;
@@ -587,8 +592,9 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             bool sel = false, s_lo = false, s_hi = false;
             if (valid) {
                 E = Rc[i];
-                int k; bool clo, chi;
-                edge_level(g, E, k, clo, chi);
+                int k = 0; bool clo = false, chi = false;
+                // only a selected edge or one that claimed in the final round needs its level
+                if ((E.flags & F_SEL) || (E.flags >> 2) == (uint32_t)r) edge_level(g, E, k, clo, chi);
                 if ((E.flags >> 2) == (uint32_t)r) {     // claimed in the final round
                     unsigned long long* cb = ((r - 1) & 1) ? g.claim1 : g.claim0;
                     if (clo) cb[E.lo] = CLAIM_FREE;
@@ -609,8 +615,8 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                         atomicAdd(&g.deg[E.lo], 1);
                         atomicAdd(&g.deg[E.hi], 1);
                         // a constrained endpoint's SD rises; with SD > k it roots the search
-                        if (clo) s_lo = atomicAdd(&g.hs[E.lo].y, 1) + 1 > k && visit(g, C, E.lo, e);
-                        if (chi) s_hi = atomicAdd(&g.hs[E.hi].y, 1) + 1 > k && visit(g, C, E.hi, e);
+                        if (clo) s_lo = atomicAdd(&g.hc[E.lo].y, 1) + 1 > k && visit(g, C, E.lo, e);
+                        if (chi) s_hi = atomicAdd(&g.hc[E.hi].y, 1) + 1 > k && visit(g, C, E.hi, e);
                     } else {
                         Bucket b = g.idx[E.bkt];
                         if (b.slo >= 0 && b.slo < g.end[E.lo] && b.shi >= 0 && b.shi < g.end[E.hi]) {
@@ -623,11 +629,11 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                         atomicSub(&g.deg[E.lo], 1);
                         atomicSub(&g.deg[E.hi], 1);
                         if (clo) {
-                            int m = atomicSub(&g.hs[E.lo].y, 1) - 1;
+                            int m = atomicSub(&g.hc[E.lo].y, 1) - 1;
                             if (m < k) { s_lo = true; g.chg[E.lo] = e; }
                         }
                         if (chi) {
-                            int m = atomicSub(&g.hs[E.hi].y, 1) - 1;
+                            int m = atomicSub(&g.hc[E.hi].y, 1) - 1;
                             if (m < k) { s_hi = true; g.chg[E.hi] = e; }
                         }
                     }
@@ -699,9 +705,10 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                 int v = 0;
                 if (i < (long long)(vq_t - vq0)) {
                     v = P.VQ[(vq0 + i) & qm];
-                    int4 h = g.hs[v];
-                    if (h.w > h.x) {
-                        g.hs[v].x = h.x + 1;
+                    const int core = g.hc[v].x;
+                    const int support = ww(g.hw[v]);
+                    if (support > core) {
+                        g.hc[v].x = core + 1;
                         g.chg[v] = e;
                         up = true;
                     }

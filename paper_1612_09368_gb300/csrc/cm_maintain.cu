@@ -68,7 +68,7 @@ __global__ void ingest_a_kernel(const int32_t* __restrict__ E, long long k, cons
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
         int32_t u = E[2 * i], v = E[2 * i + 1];
-        if (u < 0 || v < 0 || u >= g.n || v >= g.n || g.hs[u].x < 0 || g.hs[v].x < 0) {
+        if (u < 0 || v < 0 || u >= g.n || v >= g.n || g.hc[u].x < 0 || g.hc[v].x < 0) {
             atomicMin(&c->bad_index, i);
             atomicCAS(&c->error, 0, E_INVALID);
             continue;

@@ -92,7 +92,7 @@ __global__ void scatter_kernel(const int32_t* __restrict__ E, const uint32_t* __
 __global__ void set_cores_kernel(const int32_t* __restrict__ cores, DevGraph g) {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= g.n) return;
-    g.hs[v].x = cores[v];
+    g.hc[v].x = cores[v];
 }
 
 // SD(v), Definition 7: neighbours with core >= core(v).  Warp per vertex;
@@ -104,7 +104,7 @@ __global__ void set_cores_kernel(const int32_t* __restrict__ cores, DevGraph g) 
 __global__ void copy_cores_kernel(DevGraph g, int32_t* core) {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= g.n) return;
-    core[v] = g.hs[v].x;
+    core[v] = g.hc[v].x;
 }
 
 __global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1, const int32_t* __restrict__ core) {
@@ -126,7 +126,7 @@ __global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1, const int32_
             for (int q = 0; q < 4; q++) sd += c[q] >= k;
         }
         sd = warp_sum(sd);
-        if (lane == 0) g.hs[w].y = sd;
+        if (lane == 0) g.hc[w].y = sd;
     }
 }
 
@@ -266,7 +266,7 @@ __device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& 
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (w[q] >= 0 && r[q] == k + 1) {
-                g.hs[w[q]].x = k;
+                g.hc[w[q]].x = k;
                 buf[at++] = w[q];
             }
         }
@@ -298,10 +298,10 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
             const long long v = t0 + q * kPeelThreads + threadIdx.x;
             bool live = false;
             if (v < g.n) {
-                live = g.hs[v].x != -1;
+                live = g.hc[v].x != -1;
                 if (live) {
                     P.dcur[v] = g.deg[v];
-                    g.hs[v].x = UNPEELED;
+                    g.hc[v].x = UNPEELED;
                 }
             }
             const unsigned lb = __ballot_sync(0xffffffffu, live);
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
                     v = Lc[i];
                     const int d = P.dcur[v];
                     if (d == k) {
-                        g.hs[v].x = k;
+                        g.hc[v].x = k;
                         peel = true;
                     } else if (d > k) {
                         keep = true;
@@ -497,7 +497,7 @@ __global__ void validate_vertices_kernel(const int64_t* __restrict__ off, const 
         }
         for (long long j = a + lane; j < b; j += 32) {
             int32_t x = nb[j];
-            bool bad = x < 0 || x >= base + count || x == base + w || (x < base && g.hs[x].x < 0);
+            bool bad = x < 0 || x >= base + count || x == base + w || (x < base && g.hc[x].x < 0);
             if (bad) {
                 atomicMin(&c->bad_index, j);
                 atomicCAS(&c->error, 0, E_INVALID);
@@ -529,7 +529,8 @@ __global__ void init_vertices_kernel(const int64_t* __restrict__ off, int32_t co
             g.cap[v] = cp;
             g.end[v] = 0;
             g.deg[v] = 0;
-            g.hs[v] = make_int4(0, 0, 0, 0);
+            g.hc[v] = make_int2(0, 0);
+            g.hw[v] = 0ull;
             g.chg[v] = 0;
             g.taken[v] = 0;
             g.claim0[v] = CLAIM_FREE;
@@ -575,7 +576,7 @@ __global__ void validate_ids_kernel(const int32_t* __restrict__ ids, int32_t cou
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     int32_t v = ids[i];
-    if (v < 0 || v >= g.n || g.hs[v].x < 0) {
+    if (v < 0 || v >= g.n || g.hc[v].x < 0) {
         atomicMin(&c->bad_index, i);
         atomicCAS(&c->error, 0, E_INVALID);
         return;
@@ -610,7 +611,8 @@ __global__ void mark_dead_kernel(const int32_t* __restrict__ ids, int32_t count,
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     int32_t v = ids[i];
-    g.hs[v] = make_int4(-1, 0, 0, 0);
+    g.hc[v] = make_int2(-1, 0);
+    g.hw[v] = 0ull;
     g.end[v] = 0;
     g.deg[v] = 0;
 }
@@ -620,7 +622,7 @@ __global__ void mark_dead_kernel(const int32_t* __restrict__ ids, int32_t count,
 __global__ void pin_vertices_kernel(const int32_t* __restrict__ ids, int32_t count, DevGraph g) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    g.hs[ids[i]].y = PIN_SD;
+    g.hc[ids[i]].y = PIN_SD;
 }
 
 cudaError_t pin_vertices(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s) {
@@ -650,14 +652,14 @@ cudaError_t mark_dead(const int32_t* ids, int32_t count, DevGraph g, cudaStream_
 __global__ void export_cores_kernel(DevGraph g, int32_t* out) {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= g.n) return;
-    out[v] = g.hs[v].x;
+    out[v] = g.hc[v].x;
 }
 
 // SD (Definition 7) of every vertex; -1 for a deleted vertex.
 __global__ void export_sd_kernel(DevGraph g, int32_t* out) {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= g.n) return;
-    const int4 h = g.hs[v];
+    const int2 h = g.hc[v];
     out[v] = h.x < 0 ? -1 : h.y;
 }
 
@@ -743,7 +745,7 @@ __global__ void validate_pairs_kernel(const int32_t* __restrict__ E, long long k
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
         int32_t u = E[2 * i], v = E[2 * i + 1];
-        if (u < 0 || v < 0 || u >= g.n || v >= g.n || g.hs[u].x < 0 || g.hs[v].x < 0) {
+        if (u < 0 || v < 0 || u >= g.n || v >= g.n || g.hc[u].x < 0 || g.hc[v].x < 0) {
             atomicMin(&c->bad_index, ((long long)phase << 40) | i);
             atomicCAS(&c->error, 0, E_INVALID);
         }

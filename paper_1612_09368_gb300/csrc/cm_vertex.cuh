@@ -9,8 +9,9 @@
 // warp keeps four independent loads in flight per lane.  Loops are
 // warp-uniform, so warp collectives may run inside them.
 //
-// The per-iteration word of a vertex is hs.z / hs.w, read and updated as one
-// 64-bit value: z = stamp (iteration << 2 | flags), w = a count.  A word
+// The per-iteration word of a vertex is hw[v], read and updated as one
+// 64-bit value: low half z = stamp (iteration << 2 | flags), high half w = a
+// count; a scan step sees it as the z / w fields of an int4 {core, SD, z, w}.  A word
 // with an older stamp reads as "no flags, count 0"; the first update in an
 // iteration stamps it with one CAS, later updates are single atomicAdd /
 // atomicOr operations on the 64-bit word.  Insert flags: 1 visited (in a
@@ -31,7 +32,7 @@ struct LocalStats {
 // ---------------------------------------------------------------- per-iteration word
 __device__ __forceinline__ bool same_iter(uint32_t z, uint32_t e) { return (z >> 2) == e; }
 __device__ __forceinline__ unsigned long long* iter_word(const DevGraph& g, int v) {
-    return reinterpret_cast<unsigned long long*>(&g.hs[v].z);
+    return &g.hw[v];
 }
 __device__ __forceinline__ uint32_t wz(unsigned long long x) { return (uint32_t)x; }
 __device__ __forceinline__ int32_t ww(unsigned long long x) { return (int32_t)(uint32_t)(x >> 32); }
@@ -296,6 +297,25 @@ __device__ __forceinline__ void push_vertex4(Ctl* C, const MaintainParams& P, co
     if (ASYNC) __syncwarp();
 }
 
+// The words of a scan step's four neighbours as {core, SD, z, w}: core and SD
+// for every slot, then, in a second round of loads, the per-iteration word
+// only for the slots that can be candidates at level k (insert: core k and
+// SD > k; delete: core k and SD >= k); the others get z = w = 0, which no
+// body reads for a non-candidate.
+__device__ __forceinline__ void gather4(const DevGraph& g, const int (&w)[4], int k, bool del, int4 (&h)[4]) {
+    int2 c[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) c[q] = w[q] >= 0 ? g.hc[w[q]] : make_int2(-1, 0);
+    unsigned long long s[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const bool need = c[q].x == k && (del ? c[q].y >= k : c[q].y > k);
+        s[q] = need ? g.hw[w[q]] : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) h[q] = make_int4(c[q].x, c[q].y, (int)(uint32_t)s[q], (int)(uint32_t)(s[q] >> 32));
+}
+
 // Four neighbour ids of this lane for the step starting at `base` (HOLE for
 // slots at or past len).
 __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, int t0, int w[4]) {
@@ -354,7 +374,7 @@ __device__ __forceinline__ int csd_part(const DevGraph& g, int k, long long o, i
     SCANP_RANGE(Grp, o, s0, s1)
         int2 h[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? *reinterpret_cast<const int2*>(&g.hs[w[q]]) : make_int2(-1, 0);
+        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hc[w[q]] : make_int2(-1, 0);
 #pragma unroll
         for (int q = 0; q < 4; q++) pcd += (h[q].x > k) || (h[q].x == k && h[q].y > k);
     SCANP_END
@@ -368,8 +388,7 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
                                              int s0, int s1, uint32_t e) {
     SCANP_RANGE(Grp, o, s0, s1)
         int4 h[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+        gather4(g, w, k, false, h);
         bool p[4];
         unsigned long long sw[4];
 #pragma unroll
@@ -383,6 +402,43 @@ __device__ __forceinline__ void expand_range(const DevGraph& g, Ctl* C, const Ma
     SCANP_END
 }
 
+// CSD over the range (this thread's part, as csd_part) while visiting the
+// range's unvisited core-k neighbours with SD > k in the same pass: the
+// expansion of Algorithm 3 done before the vertex's support is known
+// (speculative expansion, see process_frontier).
+template <class Grp, bool ASYNC>
+__device__ __forceinline__ int csd_expand_range(const DevGraph& g, Ctl* C, const MaintainParams& P, int k,
+                                                long long o, int s0, int s1, uint32_t e) {
+    int pcd = 0;
+    SCANP_RANGE(Grp, o, s0, s1)
+        int4 h[4];
+        gather4(g, w, k, false, h);
+        bool p[4];
+        unsigned long long sw[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            pcd += (h[q].x > k) || (h[q].x == k && h[q].y > k);
+            const bool seen = same_iter((uint32_t)h[q].z, e) && ((uint32_t)h[q].z & kVisited);
+            p[q] = h[q].x == k && h[q].y > k && !seen;
+            sw[q] = word_of(h[q]);
+        }
+        visit4(g, C, w, p, e, sw);
+        push_vertex4<ASYNC>(C, P, p, w, 0, last_);
+    SCANP_END
+    return pcd;
+}
+
+// Whether a frontier vertex at level k with superior degree sd expands
+// speculatively.  CSD <= SD, so a vertex whose SD is far above k will very
+// likely rise past k and visit its candidates anyway: visiting them in the
+// CSD pass saves the second pass over its list (and, for a hub, a whole
+// round of chunk tasks).  A vertex that then turns out to stay at or below
+// k has visited vertices the paper's search would not have; they are
+// processed like any other and the result is the same, since the cores the
+// search finds do not depend on which extra vertices it visits (see the
+// design notes).
+__device__ __forceinline__ bool expand_early(int sd, int k) { return sd >= 2 * k + 2; }
+
 // InsertRemove over the range (Algorithm 4): every core-k neighbour with
 // SD > k (visited or not) loses one support; a processed one whose support
 // falls to k leaves too.
@@ -391,8 +447,7 @@ __device__ __forceinline__ void evict_ins_range(const DevGraph& g, Ctl* C, const
                                                 long long o, int s0, int s1, uint32_t e) {
     SCANP_RANGE(Grp, o, s0, s1)
         int4 h[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+        gather4(g, w, k, false, h);
         bool cand[4], p[4];
         unsigned long long sw[4];
         uint32_t of[4];
@@ -420,10 +475,8 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
         int4 h[4];
         uint32_t c[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
-            c[q] = w[q] >= 0 ? g.chg[w[q]] : 0u;
-        }
+        for (int q = 0; q < 4; q++) c[q] = w[q] >= 0 ? g.chg[w[q]] : 0u;
+        gather4(g, w, k, true, h);
         bool cand[4], p[4];
         unsigned long long sw[4];
         uint32_t of[4];
@@ -457,7 +510,9 @@ struct VInfo {
 };
 __device__ __forceinline__ VInfo load_vinfo(const DevGraph& g, int v) {
     VInfo r;
-    r.h = g.hs[v];
+    const int2 c = g.hc[v];
+    const unsigned long long x = g.hw[v];
+    r.h = make_int4(c.x, c.y, (int)(uint32_t)x, (int)(uint32_t)(x >> 32));
     r.o = g.off[v];
     r.len = g.end[v];
     return r;
@@ -478,8 +533,7 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
             int w[4];
             load4(g, o, len, lane * 4, w);
             int4 h[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hs[w[q]] : make_int4(-1, 0, 0, 0);
+            gather4(g, w, k, false, h);
             int part = 0;
 #pragma unroll
             for (int q = 0; q < 4; q++) part += (h[q].x > k) || (h[q].x == k && h[q].y > k);
@@ -511,7 +565,9 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
             return;
         }
     }
-    const int pcd = Grp::sum(csd_part<Grp>(g, k, o, 0, len));
+    const bool early = expand_early(vi.h.y, k);
+    const int pcd = Grp::sum(early ? csd_expand_range<Grp, ASYNC>(g, C, P, k, o, 0, len, e)
+                                   : csd_part<Grp>(g, k, o, 0, len));
     int32_t sup = 0;
     if (Grp::rank0()) {
         uint32_t of;
@@ -527,7 +583,7 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
         sup = Grp::sum(Grp::rank0() ? sup : 0);
     }
     if (sup > k) {
-        expand_range<Grp, ASYNC>(g, C, P, k, o, 0, len, e);
+        if (!early) expand_range<Grp, ASYNC>(g, C, P, k, o, 0, len, e);
     } else if (Grp::warp0()) {
         push_vertex<ASYNC>(C, P, lane == 0, v, 1, Grp::G == 32);
     }
@@ -554,7 +610,7 @@ __device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, c
     evict_del_range<Grp, ASYNC>(g, C, P, k, vi.o, 0, len, e);
     if constexpr (Grp::G > 32) __syncthreads();   // every warp has read k before it changes
     if (Grp::rank0()) {
-        g.hs[v].x = k - 1;
+        g.hc[v].x = k - 1;
         ls.ev++;
         ls.evl += len;
     }
@@ -563,7 +619,7 @@ __device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, c
 // SD fix-up of a vertex whose core moved in iteration e (op 0 rose, op 1 dropped).
 template <class Grp>
 __device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t e, int op, LocalStats& ls) {
-    const int kn = g.hs[v].x;
+    const int kn = g.hc[v].x;
     const long long o = g.off[v];
     const int len = g.end[v];
     const int adj_core = op == 0 ? kn : kn + 1;   // neighbours whose SD counts v differently now
@@ -573,20 +629,20 @@ __device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t 
         load4(g, o, len, t0_, w);
         int cw[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) cw[q] = w[q] >= 0 ? g.hs[w[q]].x : -1;
+        for (int q = 0; q < 4; q++) cw[q] = w[q] >= 0 ? g.hc[w[q]].x : -1;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (w[q] < 0) continue;
             sd += cw[q] >= kn;
             if (cw[q] == adj_core && g.chg[w[q]] != e) {
-                if (op == 0) atomicAdd(&g.hs[w[q]].y, 1);
-                else atomicSub(&g.hs[w[q]].y, 1);
+                if (op == 0) atomicAdd(&g.hc[w[q]].y, 1);
+                else atomicSub(&g.hc[w[q]].y, 1);
             }
         }
     SCAN4_END
     sd = Grp::sum(sd);
     if (Grp::rank0()) {
-        g.hs[v].y = sd;
+        g.hc[v].y = sd;
         ls.ch++;
         ls.chl += len;
     }
