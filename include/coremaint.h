@@ -93,7 +93,12 @@ typedef struct cm_options {
                                maximal; R > 0 = at most R rounds (still a superior edge set, perhaps
                                not a maximal one: fewer barriers per iteration, perhaps more
                                iterations).  Final cores do not depend on either choice. */
-    int32_t reserved[3];
+    int32_t expand_early;   /* insert search (Algorithm 3): a frontier vertex visits its candidates in
+                               the same pass that sums its CSD, before its support is known, when
+                               0 (default): its SD >= 2k + 2; 1: always; -1: never (the paper's order:
+                               sum first, expand only if the support exceeds k).  Visiting early can
+                               only add vertices to the search; the cores do not change. */
+    int32_t reserved[2];
 } cm_options;
 
 #define CM_SELECT_HASH 0

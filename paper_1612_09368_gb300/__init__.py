@@ -58,7 +58,7 @@ class cm_options(ctypes.Structure):
         ("debug_flags", ctypes.c_int32), ("block_mode_enter", ctypes.c_int32), ("block_mode_leave", ctypes.c_int32),
         ("hub_slots", ctypes.c_int32), ("block_slots", ctypes.c_int32), ("block_slots_delete", ctypes.c_int32),
         ("task_claim", ctypes.c_int32), ("select_order", ctypes.c_int32), ("select_rounds", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("expand_early", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 

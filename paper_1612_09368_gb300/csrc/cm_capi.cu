@@ -689,6 +689,7 @@ static MaintainParams handle_params(const cm_graph* h, int op) {
     p.claim_max = h->claim_max;
     p.sel_key = h->sel_key;
     p.sel_rounds = h->sel_rounds;
+    p.expand_early = h->opt.expand_early;
     return p;
 }
 

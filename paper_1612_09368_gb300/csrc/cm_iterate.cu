@@ -360,7 +360,7 @@ __device__ __noinline__ bool async_search(const DevGraph& g, Ctl* C, const Maint
             const VInfo vi = load_vinfo(g, v);
             const bool hub = P.hub_len > 0 && vi.len >= P.hub_len;
             if (type == T_FRONT) {
-                if (!hub || !make_hub(C, P, v, expand_early(vi.h.y, vi.h.x) ? HUB_FRONT_SPEC : HUB_FRONT, vi.h.x,
+                if (!hub || !make_hub(C, P, v, expand_early(P, vi.h.y, vi.h.x) ? HUB_FRONT_SPEC : HUB_FRONT, vi.h.x,
                                       vi.o, vi.len))
                     process_frontier<WG, true>(g, C, P, v, vi, e, ls);
             } else if (P.op == 0) {

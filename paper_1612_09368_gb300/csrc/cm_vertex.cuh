@@ -437,7 +437,9 @@ __device__ __forceinline__ int csd_expand_range(const DevGraph& g, Ctl* C, const
 // processed like any other and the result is the same, since the cores the
 // search finds do not depend on which extra vertices it visits (see the
 // design notes).
-__device__ __forceinline__ bool expand_early(int sd, int k) { return sd >= 2 * k + 2; }
+__device__ __forceinline__ bool expand_early(const MaintainParams& P, int sd, int k) {
+    return P.expand_early > 0 || (P.expand_early == 0 && sd >= 2 * k + 2);
+}
 
 // InsertRemove over the range (Algorithm 4): every core-k neighbour with
 // SD > k (visited or not) loses one support; a processed one whose support
@@ -565,7 +567,7 @@ __device__ __forceinline__ void process_frontier(const DevGraph& g, Ctl* C, cons
             return;
         }
     }
-    const bool early = expand_early(vi.h.y, k);
+    const bool early = expand_early(P, vi.h.y, k);
     const int pcd = Grp::sum(early ? csd_expand_range<Grp, ASYNC>(g, C, P, k, o, 0, len, e)
                                    : csd_part<Grp>(g, k, o, 0, len));
     int32_t sup = 0;

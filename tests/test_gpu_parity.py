@@ -160,6 +160,26 @@ def test_selection_variants(cm, order, rounds):
     _check_same(g, ref, "BA insert")
 
 
+@pytest.mark.parametrize("early", [1, -1])
+def test_expand_early_variants(cm, early):
+    """The insert search's frontier vertices visiting their candidates in
+    the CSD pass (1: always) or only after their support is known (-1: the
+    paper's order, Algorithm 3) reach the oracle's cores, SD and iteration
+    counts, on a random graph, an R-MAT graph with hubs and a single-level BA
+    graph."""
+    rng = np.random.default_rng(300 + early)
+    graphs = [(400, _rand_graph(rng, 400, 0.05)), (1 << 13, synth.rmat(13, 16, synth.stream(301))),
+              (20000, synth.ba(20000, 6, synth.stream(302)))]
+    for n, e in graphs:
+        g = cm.CoreGraph(n, _dev(e), expand_early=early)
+        ref = oracle.OracleGraph(n, e, mode=oracle.SUPERIOR)
+        for law in (synth.UNIFORM, synth.PREFERENTIAL):
+            ins = synth.static_sample_insert(n, ref.edges(), 3000, law, synth.stream(303, n, law, synth.INSERT))
+            assert g.insert_edges(_dev(ins)) == ref.insert_edges(ins)
+            assert g.stats()["iterations"] == ref.last_iterations()
+            _check_same(g, ref, f"early {early} n {n} law {law}")
+
+
 def test_cfg_er_insert_then_delete_full_size(cm):
     """ER G(n=10,000, m=50,000), 1,000 new edges inserted, then 1,000 existing
     edges deleted; cores checked after each batch (the small workload)."""
