@@ -463,7 +463,10 @@ def run_sweep(args):
             g.apply_edges(cm.CM_OP_DELETE if op == "insert" else cm.CM_OP_INSERT, dbat[j])
             g.recompute_cores()
             row.update({"repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": pst["peel_levels"],
-                        "peel_subwaves": pst["waves"],
+                        "peel_subwaves": pst["waves"], "peel_barriers": pst["barriers"],
+                        "peel_phase_ms": {"scan": pst["phase_ns"]["claim"] / 1e6,
+                                          "subwaves": pst["phase_ns"]["check"] / 1e6,
+                                          "chunks": pst["phase_ns"]["apply"] / 1e6},
                         "peel_ms": pst["maintain_ms"], "peel_alg_bytes": pst["alg_bytes"], "peel_gbs": pg,
                         "peel_frac": pg / peak})
         per_case.append(row)

@@ -93,11 +93,11 @@ typedef struct cm_options {
                                maximal; R > 0 = at most R rounds (still a superior edge set, perhaps
                                not a maximal one: fewer barriers per iteration, perhaps more
                                iterations).  Final cores do not depend on either choice. */
-    int32_t expand_early;   /* insert search (Algorithm 3): a frontier vertex visits its candidates in
-                               the same pass that sums its CSD, before its support is known, when
-                               0 (default): its SD >= 2k + 2; 1: always; -1: never (the paper's order:
-                               sum first, expand only if the support exceeds k).  Visiting early can
-                               only add vertices to the search; the cores do not change. */
+    int32_t expand_early;   /* insert search (Algorithm 3): 0 (default) or 1 = a frontier vertex visits
+                               its candidates in the same pass that sums its CSD, before its support
+                               is known; -1 = the paper's order (sum first, expand only if the
+                               support exceeds k).  Visiting early can only add vertices to the
+                               search; the cores do not change. */
     int32_t reserved[2];
 } cm_options;
 
@@ -139,7 +139,9 @@ typedef struct cm_stats {
     int64_t peel_levels;     /* cm_recompute_cores / cm_create: peeling levels */
     int64_t barriers;        /* barriers executed by the maintenance launches */
     int64_t grid_iterations; /* iterations run grid-wide (the rest ran in one block) */
-    int64_t phase_ns[7];     /* device time per phase: claim, check, apply, discover, evict, commit, fix-up */
+    int64_t phase_ns[7];     /* device time per phase: claim, check, apply, discover, evict, commit, fix-up;
+                                for cm_recompute_cores / cm_create: level scans, sub-waves, chunk phases
+                                of the peel (the rest zero) */
     int64_t reserved[4];
 } cm_stats;
 

@@ -44,7 +44,7 @@ struct MaintainParams {
     int32_t sel_rounds;       // claim rounds per iteration (0 = until the set is maximal)
     int32_t use_cond;         // inside a captured step: the single-block kernel drives the loop node
     int32_t phantom_task;     // test hook: every grid search counts one task that is never queued
-    int32_t expand_early;     // frontier expansion in the CSD pass: 0 when SD >= 2k+2, 1 always, -1 never
+    int32_t expand_early;     // frontier expansion in the CSD pass: >= 0 yes (default), -1 after it (paper's order)
     int32_t pad_;
     unsigned long long cond;  // that node's conditional handle
 };

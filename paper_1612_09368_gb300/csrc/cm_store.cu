@@ -276,6 +276,25 @@ __device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& 
     }
 }
 
+// Phases of the peel timed at its barriers (block 0's view, into Ctl::ph):
+// the level scans, the sub-waves and the chunk phases.
+enum { PP_SCAN = 0, PP_WAVE = 1, PP_CHUNK = 2 };
+struct PeelClock {
+    Ctl* c;
+    unsigned long long t;
+    bool on;
+    __device__ bool sync(const PeelParams& P, int phase) {
+        const bool ok = grid_sync(c, P.expect, P.limit_ns);
+        if (on) {
+            const unsigned long long now = gtimer();
+            c->ph[phase] += now - t;
+            c->st[ST_BARRIERS] += 1;
+            t = now;
+        }
+        return ok;
+    }
+};
+
 __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
     Ctl* C = P.ctl;
     const DevGraph g = P.g;
@@ -288,6 +307,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
     int32_t* buf = S.buf[wib];
     int cnt = 0;
     bool ok;
+    PeelClock clk{C, gtimer(), blockIdx.x == 0 && threadIdx.x == 0};
     // live vertices start unpeeled with their live degree (compacted into
     // the remaining list a tile at a time, like the level scans below)
     for (long long t0 = (long long)blockIdx.x * kScanTile; t0 < g.n; t0 += (long long)gridDim.x * kScanTile) {
@@ -316,7 +336,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
         for (int j = threadIdx.x; j < S.nkeep; j += kPeelThreads) P.L0[S.kbase + j] = S.keep[j];
         __syncthreads();
     }
-    if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+    if (!(ok = clk.sync(P, PP_SCAN))) return;
     unsigned long long nl = vload64(&C->spc[1]);
     int32_t* Lc = P.L0;
     int32_t* Ln = P.L1;
@@ -379,7 +399,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
             for (int j = threadIdx.x; j < S.npeel; j += kPeelThreads) P.F[S.pbase + j] = S.peel[j];
             __syncthreads();
         }
-        if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+        if (!(ok = clk.sync(P, PP_SCAN))) return;
         unsigned long long fhi = vload64(&C->stail[0]);
         unsigned long long nln = vload64(&C->spc[1]);
         unsigned long long smx = vload64(&C->spc[3]);
@@ -421,7 +441,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
                 peel_range(g, P, C, o, 0, len, k, buf, cnt);
             }
             block_flush_peeled(C, P, S, cnt);
-            if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+            if (!(ok = clk.sync(P, PP_WAVE))) return;
             const unsigned long long nchunks = min(vload64(&C->spc[3]), P.chunk_cap);
             if (nchunks > 0) {
                 for (unsigned long long c = (unsigned long long)gwarp; c < nchunks; c += (unsigned long long)nwarps) {
@@ -432,7 +452,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
                     peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k, buf, cnt);
                 }
                 block_flush_peeled(C, P, S, cnt);
-                if (!(ok = grid_sync(C, P.expect, P.limit_ns))) return;
+                if (!(ok = clk.sync(P, PP_CHUNK))) return;
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
             lo = hi;
