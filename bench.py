@@ -463,9 +463,10 @@ def run_sweep(args):
             g.apply_edges(cm.CM_OP_DELETE if op == "insert" else cm.CM_OP_INSERT, dbat[j])
             g.recompute_cores()
             row.update({"repeel_ms": rp, "speedup_vs_repeel": rp / call_ms, "peel_levels": pst["peel_levels"],
-                        "peel_cascades": pst["waves"], "peel_barriers": pst["barriers"],
+                        "peel_subwaves": pst["waves"], "peel_barriers": pst["barriers"],
                         "peel_phase_ms": {"scan": pst["phase_ns"]["claim"] / 1e6,
-                                          "cascade": pst["phase_ns"]["check"] / 1e6},
+                                          "subwaves": pst["phase_ns"]["check"] / 1e6,
+                                          "chunks": pst["phase_ns"]["apply"] / 1e6},
                         "peel_ms": pst["maintain_ms"], "peel_alg_bytes": pst["alg_bytes"], "peel_gbs": pg,
                         "peel_frac": pg / peak})
         per_case.append(row)
@@ -1206,7 +1207,7 @@ def run_rounds(args):
         pk, _ = load_peaks()
         pgbs = pst["alg_bytes"] / (pst["maintain_ms"] / 1000.0) / 1e9 if pst["maintain_ms"] else 0.0
         repeel = {"repeel_ms": rp_ms, "maintain_insert_1e4_ms_median": mi, "speedup": rp_ms / mi,
-                  "peel_levels": pst["peel_levels"], "peel_cascades": pst["waves"],
+                  "peel_levels": pst["peel_levels"], "peel_subwaves": pst["waves"],
                   "peel_roofline": {"peel_and_sd_ms": pst["maintain_ms"], "alg_bytes": pst["alg_bytes"],
                                     "achieved_gbs": pgbs, "frac": pgbs / pk if pk else None}}
 

@@ -140,8 +140,8 @@ typedef struct cm_stats {
     int64_t barriers;        /* barriers executed by the maintenance launches */
     int64_t grid_iterations; /* iterations run grid-wide (the rest ran in one block) */
     int64_t phase_ns[7];     /* device time per phase: claim, check, apply, discover, evict, commit, fix-up;
-                                for cm_recompute_cores / cm_create: the peel's level scans and level
-                                cascades (the rest zero) */
+                                for cm_recompute_cores / cm_create: level scans, sub-waves, chunk phases
+                                of the peel (the rest zero) */
     int64_t reserved[4];
 } cm_stats;
 

@@ -582,8 +582,8 @@ static int peel_all(cm_graph* h) {
     h->last.peel_levels = (int64_t)h->hctl->st[ST_LEVELS];
     h->last.waves = (int64_t)h->hctl->st[ST_WAVES];   // sub-waves of the peel
     h->last.barriers = (int64_t)h->hctl->st[ST_BARRIERS];
-    // phase times of the peel: level scans, cascades
-    for (int i = 0; i < 2; i++) h->last.phase_ns[i] = (int64_t)h->hctl->ph[i];
+    // phase times of the peel: level scans, sub-waves, chunk phases
+    for (int i = 0; i < 3; i++) h->last.phase_ns[i] = (int64_t)h->hctl->ph[i];
     // Algorithmic bytes of the peel: 16 B per vertex to start it (degree
     // read, working degree, core and list writes); 12 B per remaining-list
     // entry scanned at a level (id, working degree, list write); 12 B per

@@ -436,11 +436,8 @@ __device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long lon
     }
     const unsigned long long prio = edge_prio(E, by_key);
     unsigned long long* cb = (r & 1) ? g.claim1 : g.claim0;
-    // a claim already below this edge's priority means it cannot win there:
-    // skip the atomic (a hub shared by thousands of batch edges would
-    // otherwise serialise thousands of atomics on one word per round)
-    if (clo && vload64(&cb[E.lo]) > prio) atomicMin(&cb[E.lo], prio);
-    if (chi && vload64(&cb[E.hi]) > prio) atomicMin(&cb[E.hi], prio);
+    if (clo) atomicMin(&cb[E.lo], prio);
+    if (chi) atomicMin(&cb[E.hi], prio);
     R[i].flags = (f & 3u) | ((uint32_t)(r + 1) << 2);
 }
 

@@ -176,30 +176,24 @@ cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, int32_t* core_scratch, 
 // scan reads the working degree alone (never the 16-byte vertex word) to
 // tell the three cases apart.
 //
-// After a level's scan, the departures at that level cascade without
-// barriers: every vertex that leaves (found by the scan, or brought to k by
-// a decrement) is a task in the frontier ring F, and warps claim tasks until
-// the level is quiescent (every task queued has finished), as the
-// maintenance search does (cm_iterate.cu).  A task scans its vertex's list
-// and decrements the neighbours; a neighbour that reaches k joins F.  F
-// slots start empty (-1) and each is written once with a volatile store; a
-// warp that claimed a slot not written yet waits for it, with a bounded
-// wait.  A departure with at least kPeelBig slots becomes kPeelChunk-slot
-// chunk tasks instead (F entries -3 - i naming P.chunks[i]), so a hub's
-// list is spread over many warps.  One grid barrier ends each level.  The
-// order of a level's departures does not change which vertices leave at it.
+// A frontier vertex with at least kPeelBig slots is not scanned by the warp
+// that takes it: its list is cut into kPeelChunk-slot chunk tasks that every
+// warp takes after a barrier, so one high-degree vertex does not hold a whole
+// sub-wave on a single warp.
 //
 // No counter is shared by the whole grid per vertex: the level scan
 // compacts a tile of kScanTile entries per block in shared memory and
-// appends it with one atomic per list; warps claim up to kPeelClaim tasks
-// with one atomic, collect departures in a per-warp buffer that reaches F
-// with one atomic per flush, and report finished tasks in batches.
+// appends it with one atomic per list; frontier vertices and chunk tasks
+// are dealt to warps by index, not claimed; and the vertices a sub-wave
+// peels collect in a per-warp shared buffer that reaches the frontier ring
+// with one atomic per flush.  (With one atomic per warp per step on a few
+// counters, the serialised atomics at those counters were most of the
+// peel's time.)
 constexpr int kPeelThreads = 512;
 constexpr int kPeelWarps = kPeelThreads / 32;
 constexpr int kPeelBig = 2048;
 constexpr int kPeelChunk = 512;
-constexpr int kPeelClaim = 16;                // most tasks a warp claims at once
-constexpr int32_t kFEmpty = -1;               // an F slot not written yet
+constexpr unsigned long long kPeelNoTask = ~0ull;
 constexpr int kScanTile = 4 * kPeelThreads;   // list entries per block and scan step
 constexpr int kPushBuf = 256;                 // per-warp buffer of peeled vertices
 constexpr int kPushFlush = kPushBuf - 128;    // a scan step adds at most 128
@@ -209,21 +203,36 @@ struct PeelShared {
     int32_t peel[kScanTile];            // level scan: vertices of degree k
     int32_t buf[kPeelWarps][kPushBuf];  // sub-waves: peeled vertices per warp
     int wcnt[kPeelWarps];
-    volatile int quiet;                 // the level whose cascade this block's poller found quiescent
     int nkeep, npeel, mx;
     unsigned long long kbase, pbase, wbase;
 };
 
 // Appends the warp's buffered vertices to the frontier ring (one atomic).
-// The entries are stored volatile: warps of the cascade below spin on the
-// slots they claimed until the entry appears.
 __device__ __forceinline__ void flush_peeled(Ctl* C, const PeelParams& P, int32_t* buf, int& cnt) {
     if (cnt == 0) return;
     unsigned long long b = 0;
     if (lane_id() == 0) b = atomicAdd(&C->tail[0], (unsigned long long)cnt);
     b = __shfl_sync(0xffffffffu, b, 0);
-    for (int i = lane_id(); i < cnt; i += 32) *(volatile int32_t*)&P.F[b + i] = buf[i];
+    for (int i = lane_id(); i < cnt; i += 32) P.F[b + i] = buf[i];
     __syncwarp();
+    cnt = 0;
+}
+
+// End of a sub-wave: the block's warps append their buffers to the frontier
+// ring together, with one atomic.  Every thread of the block calls it.
+__device__ __forceinline__ void block_flush_peeled(Ctl* C, const PeelParams& P, PeelShared& S, int& cnt) {
+    const int wib = threadIdx.x >> 5;
+    if (lane_id() == 0) S.wcnt[wib] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int i = 0; i < kPeelWarps; i++) tot += S.wcnt[i];
+        S.wbase = tot ? atomicAdd(&C->tail[0], (unsigned long long)tot) : 0;
+    }
+    __syncthreads();
+    int pre = 0;
+    for (int i = 0; i < wib; i++) pre += S.wcnt[i];
+    for (int i = lane_id(); i < cnt; i += 32) P.F[S.wbase + pre + i] = S.buf[wib][i];
     cnt = 0;
 }
 
@@ -267,134 +276,9 @@ __device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& 
     }
 }
 
-// One departure of the cascade at level k: its list is scanned by this warp,
-// or, with at least kPeelBig slots, queued as chunk tasks for all warps
-// (the descriptors first, then, after a fence, the F entries naming them).
-// Chunk tasks are limited so that F (n vertices at most, plus the chunk
-// entries) never overflows; past the limit the warp scans the list itself.
-// Warp-collective.
-__device__ __forceinline__ void cascade_vertex(const DevGraph& g, const PeelParams& P, Ctl* C, int v, int k,
-                                               int32_t* buf, int& cnt, long long& slots) {
-    const int lane = lane_id();
-    const long long o = g.off[v];
-    const int len = g.end[v];
-    slots += len;
-    if (len >= kPeelBig) {
-        const int nch = (len + kPeelChunk - 1) / kPeelChunk;
-        const unsigned long long fcap = P.qmask + 1;
-        const unsigned long long room =
-            fcap > (unsigned long long)g.n + 64 ? min(P.chunk_cap, fcap - (unsigned long long)g.n - 64) : 0ull;
-        unsigned long long cb = 0, tb = 0;
-        int fits = 0;
-        if (lane == 0) {
-            cb = atomicAdd(&C->hub_created, (unsigned long long)nch);
-            fits = cb + nch <= room;
-        }
-        fits = __shfl_sync(0xffffffffu, fits, 0);
-        if (fits) {
-            cb = __shfl_sync(0xffffffffu, cb, 0);
-            for (int c = lane; c < nch; c += 32)
-                P.chunks[cb + c] = ((unsigned long long)(uint32_t)v << 32) | (uint32_t)c;
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) tb = atomicAdd(&C->tail[0], (unsigned long long)nch);
-            tb = __shfl_sync(0xffffffffu, tb, 0);
-            for (int c = lane; c < nch; c += 32) *(volatile int32_t*)&P.F[tb + c] = (int32_t)(-3 - (long long)(cb + c));
-            __syncwarp();
-            return;
-        }
-    }
-    peel_range(g, P, C, o, 0, len, k, buf, cnt);
-}
-
-// The cascade of level k: tasks are F[f0, ...) until quiescence.  A warp
-// claims up to kPeelClaim consecutive slots with one atomic (doubling while
-// its slots are ready, back to one after a wait).  Before it waits it
-// flushes its departures and reports its finished tasks, so a waiting warp
-// never holds back the quiescence test (finished == queued); one warp per
-// block polls the counters and tells the others through shared memory.
-// Every wait is bounded by limit_ns.  Returns false on error.
-__device__ __noinline__ bool peel_cascade(const DevGraph& g, const PeelParams& P, Ctl* C, PeelShared& S, int k,
-                                          unsigned long long f0, int tag, int32_t* buf, int& cnt, long long& slots) {
-    const int lane = lane_id();
-    const bool poller = threadIdx.x < 32;
-    const unsigned long long fcap = P.qmask + 1;
-    const unsigned long long t_start = gtimer();
-    unsigned long long idx = 0, ndone = 0;
-    int left = 0, claim = 1;
-    bool waited = false;
-    for (;;) {
-        int32_t x = kFEmpty;
-        if (lane == 0) {
-            if (left == 0) {
-                claim = waited ? 1 : min(2 * claim, kPeelClaim);
-                waited = false;
-                idx = atomicAdd(&C->task_head, (unsigned long long)claim);
-                left = claim;
-            }
-            if (idx < fcap) x = *(volatile int32_t*)&P.F[idx];
-        }
-        x = __shfl_sync(0xffffffffu, x, 0);
-        if (x == kFEmpty) {
-            // nothing ready: make this warp's work visible, then wait
-            flush_peeled(C, P, buf, cnt);
-            int quit = 0;
-            if (lane == 0) {
-                if (ndone) {
-                    __threadfence();
-                    atomicAdd(&C->task_done, ndone);
-                    ndone = 0;
-                }
-                waited = true;
-                unsigned int nap = 32;
-                for (unsigned int spins = 0;; spins++) {
-                    if (idx < fcap) {
-                        x = *(volatile int32_t*)&P.F[idx];
-                        if (x != kFEmpty) break;
-                    }
-                    if (poller) {
-                        const unsigned long long d = vload64(&C->task_done);
-                        if (d == vload64(&C->tail[0]) - f0 || vload32(&C->error)) {
-                            S.quiet = tag;
-                            quit = 1;
-                            break;
-                        }
-                    } else if (S.quiet == tag) {
-                        quit = 1;
-                        break;
-                    }
-                    if ((spins & 3u) == 0 && gtimer() - t_start > P.limit_ns) {
-                        atomicCAS(&C->error, 0, E_BARRIER_TIMEOUT);
-                        quit = 1;
-                        break;
-                    }
-                    __nanosleep(nap);
-                    if (nap < 512) nap <<= 1;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, quit, 0)) break;
-            x = __shfl_sync(0xffffffffu, x, 0);
-        }
-        if (lane == 0) {
-            idx++;
-            left--;
-        }
-        if (x >= 0) {
-            cascade_vertex(g, P, C, x, k, buf, cnt, slots);
-        } else if (x <= -3) {   // a chunk task: its descriptor was written before its entry
-            const unsigned long long t = vload64(&P.chunks[(unsigned long long)(-3 - (long long)x)]);
-            const int v = (int)(t >> 32);
-            const int s0 = (int)(t & 0xFFFFFFFFu) * kPeelChunk;
-            peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k, buf, cnt);
-        }
-        if (lane == 0) ndone++;
-    }
-    return vload32(&C->error) == 0;
-}
-
 // Phases of the peel timed at its barriers (block 0's view, into Ctl::ph):
-// the level scans and the cascades.
-enum { PP_SCAN = 0, PP_WAVE = 1 };
+// the level scans, the sub-waves and the chunk phases.
+enum { PP_SCAN = 0, PP_WAVE = 1, PP_CHUNK = 2 };
 struct PeelClock {
     Ctl* c;
     unsigned long long t;
@@ -419,18 +303,11 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
     const int wib = threadIdx.x >> 5;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
     int32_t* buf = S.buf[wib];
     int cnt = 0;
     bool ok;
     PeelClock clk{C, gtimer(), blockIdx.x == 0 && threadIdx.x == 0};
-    // every F slot starts empty; cascade tasks start at slot 0; no level is quiescent yet
-    for (long long i = gtid; i < (long long)(P.qmask + 1); i += nthr) P.F[i] = kFEmpty;
-    if (threadIdx.x == 0) S.quiet = -1;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        C->task_head = 0;
-        C->task_done = 0;
-        C->hub_created = 0;
-    }
     // live vertices start unpeeled with their live degree (compacted into
     // the remaining list a tile at a time, like the level scans below)
     for (long long t0 = (long long)blockIdx.x * kScanTile; t0 < g.n; t0 += (long long)gridDim.x * kScanTile) {
@@ -535,21 +412,55 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
             k = 0x7FFFFFFF - (int)smx;   // jump to the smallest remaining degree
             continue;
         }
-        // the cascade of level k.  A peeled neighbour needs no test: its
+        // sub-waves at level k.  A peeled neighbour needs no test: its
         // working degree is at most k when it leaves and only falls after,
         // so a decrement can bring exactly k + 1 down to k only for a
         // vertex still in the graph.
-        ok = peel_cascade(g, P, C, S, k, f0, (int)levels, buf, cnt, slots);
-        if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
-        if (!(ok = clk.sync(P, PP_WAVE) && ok)) return;
-        ft = vload64(&C->stail[0]);
+        unsigned long long lo = f0, hi = fhi;
+        while (hi > lo) {
+            const unsigned long long cnt_f = hi - lo;
+            for (unsigned long long j = (unsigned long long)gwarp; j < cnt_f; j += (unsigned long long)nwarps) {
+                const int v = P.F[lo + j];
+                const long long o = g.off[v];
+                const int len = g.end[v];
+                slots += len;
+                if (len >= kPeelBig) {
+                    // chunk tasks (vertex, chunk), run by every warp after the barrier
+                    const int nch = (len + kPeelChunk - 1) / kPeelChunk;
+                    unsigned long long tb = 0;
+                    if (lane == 0) tb = atomicAdd(&C->pc[3], (unsigned long long)nch);
+                    tb = __shfl_sync(0xffffffffu, tb, 0);
+                    const bool fits = tb + nch <= P.chunk_cap;
+                    for (int c = lane; c < nch; c += 32) {
+                        if (tb + c >= P.chunk_cap) break;
+                        P.chunks[tb + c] = fits ? (((unsigned long long)(uint32_t)v << 32) | (uint32_t)c)
+                                                : kPeelNoTask;
+                    }
+                    if (fits) continue;
+                }
+                peel_range(g, P, C, o, 0, len, k, buf, cnt);
+            }
+            block_flush_peeled(C, P, S, cnt);
+            if (!(ok = clk.sync(P, PP_WAVE))) return;
+            const unsigned long long nchunks = min(vload64(&C->spc[3]), P.chunk_cap);
+            if (nchunks > 0) {
+                for (unsigned long long c = (unsigned long long)gwarp; c < nchunks; c += (unsigned long long)nwarps) {
+                    const unsigned long long task = P.chunks[c];
+                    if (task == kPeelNoTask) continue;
+                    const int v = (int)(task >> 32);
+                    const int s0 = (int)(task & 0xFFFFFFFFu) * kPeelChunk;
+                    peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k, buf, cnt);
+                }
+                block_flush_peeled(C, P, S, cnt);
+                if (!(ok = clk.sync(P, PP_CHUNK))) return;
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
+            lo = hi;
+            hi = vload64(&C->stail[0]);
+        }
+        ft = hi;
         k++;
         levels++;
-        // the next level's tasks start where this level's ended
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            C->task_head = ft;
-            C->task_done = 0;
-        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_LEVELS] = (unsigned long long)levels;
     if (lane == 0 && slots) atomicAdd(&C->st[ST_VISSLOTS], (unsigned long long)slots);
