@@ -187,6 +187,7 @@ static int grow_vertices(cm_graph* h, int32_t need) {
     DevGraph& g = h->g;
     size_t oc = (size_t)h->ncap;
     bool ok = realloc_dev(h, g.hc, oc, nc, keep) && realloc_dev(h, g.hw, oc, nc, keep) &&
+              realloc_dev(h, g.kc, oc, nc, keep) &&
               realloc_dev(h, g.off, oc, nc, keep) &&
               realloc_dev(h, g.end, oc, nc, keep) && realloc_dev(h, g.cap, oc, nc, keep) &&
               realloc_dev(h, g.deg, oc, nc, keep) && realloc_dev(h, g.chg, oc, nc, keep) &&
@@ -196,6 +197,7 @@ static int grow_vertices(cm_graph* h, int32_t need) {
     size_t tail = (size_t)(nc - keep);
     CK(h, cudaMemsetAsync(g.hc + keep, 0, tail * sizeof(int2), h->stream));
     CK(h, cudaMemsetAsync(g.hw + keep, 0, tail * sizeof(unsigned long long), h->stream));
+    CK(h, cudaMemsetAsync(g.kc + keep, 0, tail * sizeof(uint32_t), h->stream));
     CK(h, cudaMemsetAsync(g.end + keep, 0, tail * sizeof(int32_t), h->stream));
     CK(h, cudaMemsetAsync(g.cap + keep, 0, tail * sizeof(int32_t), h->stream));
     CK(h, cudaMemsetAsync(g.deg + keep, 0, tail * sizeof(int32_t), h->stream));
@@ -367,6 +369,7 @@ static void free_all(cm_graph* h) {
     size_t nc = (size_t)h->ncap;
     dfree(h, g.hc, nc * sizeof(int2));
     dfree(h, g.hw, nc * sizeof(unsigned long long));
+    dfree(h, g.kc, nc * sizeof(uint32_t));
     dfree(h, g.off, nc * 8);
     dfree(h, g.end, nc * 4);
     dfree(h, g.cap, nc * 4);
@@ -1721,7 +1724,7 @@ extern "C" int cm_step_run(cm_step* s, const int64_t* ins_counts, const int32_t*
 // are restored, so each trial replays the same work from the same graph.
 struct Snapshot {
     size_t nv = 0, adj = 0, idx = 0;
-    unsigned char* words = nullptr;   // hc then hw (16 bytes per vertex)
+    unsigned char* words = nullptr;   // hc, hw, then kc (20 bytes per vertex)
     int64_t* off = nullptr;
     int32_t* i32 = nullptr;        // end, cap, deg, chg, taken (5 x nv)
     unsigned long long* claims = nullptr;   // claim0, claim1 (2 x nv)
@@ -1734,7 +1737,7 @@ struct Snapshot {
 };
 
 static void snap_free(cm_graph* h, Snapshot& z) {
-    dfree(h, z.words, z.nv * 16);
+    dfree(h, z.words, z.nv * 20);
     dfree(h, z.off, z.nv * 8);
     dfree(h, z.i32, z.nv * 4 * 5);
     dfree(h, z.claims, z.nv * 8 * 2);
@@ -1754,6 +1757,7 @@ static int snap_copy(cm_graph* h, Snapshot& z, bool save) {
     const size_t nv = z.nv;
     CK(h, cp(z.words, g.hc, nv * 8));
     CK(h, cp(z.words + nv * 8, g.hw, nv * 8));
+    CK(h, cp(z.words + nv * 16, g.kc, nv * 4));
     CK(h, cp(z.off, g.off, nv * 8));
     CK(h, cp(z.i32 + 0 * nv, g.end, nv * 4));
     CK(h, cp(z.i32 + 1 * nv, g.cap, nv * 4));
@@ -1787,7 +1791,7 @@ static int snap_take(cm_graph* h, Snapshot& z) {
     z.nv = (size_t)h->n;
     z.adj = (size_t)h->hctl->adj_top;
     z.idx = (size_t)h->idx_size;
-    z.words = (unsigned char*)dalloc(h, z.nv * 16);
+    z.words = (unsigned char*)dalloc(h, z.nv * 20);
     z.off = (int64_t*)dalloc(h, z.nv * 8);
     z.i32 = (int32_t*)dalloc(h, z.nv * 4 * 5);
     z.claims = (unsigned long long*)dalloc(h, z.nv * 8 * 2);

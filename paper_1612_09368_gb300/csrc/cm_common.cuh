@@ -11,6 +11,12 @@
 //           | flags), high 32 bits a count (insert: visited / processed
 //           flags and support; delete: evicted-neighbour count).  Scans load
 //           it only for the neighbours that can be candidates at their level.
+//   kc[v]   u32   core(v) << 1 | (SD(v) > core(v)): all an insert scan needs
+//           to know of a neighbour besides its per-iteration word (CSD,
+//           Definition 8, counts neighbours above k and core-k neighbours
+//           with SD > k; the candidates are the latter).  4 bytes per vertex:
+//           at 2^24 vertices the array (67 MB) fits in L2.  Every write of a
+//           core or an SD updates it (see key_of and its callers).
 //   off[v]  int64 first adjacency slot; end[v] used slots (live + holes);
 //   cap[v]  allocated slots (multiple of 4, so lists start 16-byte aligned);
 //   deg[v]  live degree.  adj[] holds neighbour ids, HOLE (-1) for a deleted
@@ -161,6 +167,7 @@ struct DevGraph {
     int32_t pad;
     int2* hc;
     unsigned long long* hw;
+    uint32_t* kc;
     int64_t* off;
     int32_t* end;
     int32_t* cap;
@@ -175,6 +182,14 @@ struct DevGraph {
     unsigned long long idx_mask;
     int64_t adj_cap;
 };
+
+// The insert-scan key of a vertex with core `core` and superior degree sd;
+// a dead vertex (core -1) reads back as core -1.
+__device__ __forceinline__ uint32_t key_of(int core, int sd) {
+    return ((uint32_t)core << 1) | (sd > core ? 1u : 0u);
+}
+__device__ __forceinline__ int key_core(uint32_t key) { return (int32_t)key >> 1; }
+constexpr uint32_t KEY_DEAD = 0xFFFFFFFFu;
 
 // ---------------------------------------------------------------- hashing
 // MurmurHash3 64-bit finaliser (Appleby, public domain): a bijection, used

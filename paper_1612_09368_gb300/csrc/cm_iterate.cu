@@ -255,7 +255,10 @@ __device__ __forceinline__ void run_chunk(const DevGraph& g, Ctl* C, const Maint
     if (lane == 0) {
         __threadfence();
         if (atomicAdd(&it->done, 1u) == (uint32_t)(nch - 1)) {
-            if (kind == HUB_EVICT_DEL) g.hc[v].x = k - 1;
+            if (kind == HUB_EVICT_DEL) {
+                g.hc[v].x = k - 1;
+                g.kc[v] = key_of(k - 1, 0);   // the SD fix-up of the next claim phase sets its bit
+            }
             if (kind != HUB_EXPAND) {
                 ls.ev++;
                 ls.evl += len;
@@ -615,8 +618,18 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                         atomicAdd(&g.deg[E.lo], 1);
                         atomicAdd(&g.deg[E.hi], 1);
                         // a constrained endpoint's SD rises; with SD > k it roots the search
-                        if (clo) s_lo = atomicAdd(&g.hc[E.lo].y, 1) + 1 > k && visit(g, C, E.lo, e);
-                        if (chi) s_hi = atomicAdd(&g.hc[E.hi].y, 1) + 1 > k && visit(g, C, E.hi, e);
+                        // (one selected edge per constrained endpoint and level: this is the
+                        // only SD change of the endpoint in APPLY, so its key bit follows it)
+                        if (clo) {
+                            const int sd = atomicAdd(&g.hc[E.lo].y, 1) + 1;
+                            if (sd > k) atomicOr(&g.kc[E.lo], 1u);
+                            s_lo = sd > k && visit(g, C, E.lo, e);
+                        }
+                        if (chi) {
+                            const int sd = atomicAdd(&g.hc[E.hi].y, 1) + 1;
+                            if (sd > k) atomicOr(&g.kc[E.hi], 1u);
+                            s_hi = sd > k && visit(g, C, E.hi, e);
+                        }
                     } else {
                         Bucket b = g.idx[E.bkt];
                         if (b.slo >= 0 && b.slo < g.end[E.lo] && b.shi >= 0 && b.shi < g.end[E.hi]) {
@@ -630,10 +643,12 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                         atomicSub(&g.deg[E.hi], 1);
                         if (clo) {
                             int m = atomicSub(&g.hc[E.lo].y, 1) - 1;
+                            if (m <= k) atomicAnd(&g.kc[E.lo], ~1u);
                             if (m < k) { s_lo = true; g.chg[E.lo] = e; }
                         }
                         if (chi) {
                             int m = atomicSub(&g.hc[E.hi].y, 1) - 1;
+                            if (m <= k) atomicAnd(&g.kc[E.hi], ~1u);
                             if (m < k) { s_hi = true; g.chg[E.hi] = e; }
                         }
                     }
@@ -709,6 +724,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                     const int support = ww(g.hw[v]);
                     if (support > core) {
                         g.hc[v].x = core + 1;
+                        g.kc[v] = key_of(core + 1, 0);   // bit set by the SD fix-up
                         g.chg[v] = e;
                         up = true;
                     }

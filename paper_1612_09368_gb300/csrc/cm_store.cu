@@ -126,7 +126,10 @@ __global__ void init_mcd_kernel(DevGraph g, int32_t v0, int32_t v1, const int32_
             for (int q = 0; q < 4; q++) sd += c[q] >= k;
         }
         sd = warp_sum(sd);
-        if (lane == 0) g.hc[w].y = sd;
+        if (lane == 0) {
+            g.hc[w].y = sd;
+            g.kc[w] = key_of(k, sd);
+        }
     }
 }
 
@@ -550,6 +553,7 @@ __global__ void init_vertices_kernel(const int64_t* __restrict__ off, int32_t co
             g.end[v] = 0;
             g.deg[v] = 0;
             g.hc[v] = make_int2(0, 0);
+            g.kc[v] = key_of(0, 0);
             g.hw[v] = 0ull;
             g.chg[v] = 0;
             g.taken[v] = 0;
@@ -632,6 +636,7 @@ __global__ void mark_dead_kernel(const int32_t* __restrict__ ids, int32_t count,
     if (i >= count) return;
     int32_t v = ids[i];
     g.hc[v] = make_int2(-1, 0);
+    g.kc[v] = KEY_DEAD;
     g.hw[v] = 0ull;
     g.end[v] = 0;
     g.deg[v] = 0;
@@ -643,6 +648,7 @@ __global__ void pin_vertices_kernel(const int32_t* __restrict__ ids, int32_t cou
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     g.hc[ids[i]].y = PIN_SD;
+    atomicOr(&g.kc[ids[i]], 1u);
 }
 
 cudaError_t pin_vertices(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s) {

@@ -304,8 +304,16 @@ __device__ __forceinline__ void push_vertex4(Ctl* C, const MaintainParams& P, co
 // body reads for a non-candidate.
 __device__ __forceinline__ void gather4(const DevGraph& g, const int (&w)[4], int k, bool del, int4 (&h)[4]) {
     int2 c[4];
+    if (del) {   // deletion needs the exact SD (its threshold is SD - k + 1)
 #pragma unroll
-    for (int q = 0; q < 4; q++) c[q] = w[q] >= 0 ? g.hc[w[q]] : make_int2(-1, 0);
+        for (int q = 0; q < 4; q++) c[q] = w[q] >= 0 ? g.hc[w[q]] : make_int2(-1, 0);
+    } else {     // insertion needs core and whether SD > core: the 4-byte key, SD as core + that bit
+        uint32_t key[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) key[q] = w[q] >= 0 ? g.kc[w[q]] : KEY_DEAD;
+#pragma unroll
+        for (int q = 0; q < 4; q++) c[q] = make_int2(key_core(key[q]), key_core(key[q]) + (int)(key[q] & 1u));
+    }
     unsigned long long s[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -372,11 +380,11 @@ template <class Grp>
 __device__ __forceinline__ int csd_part(const DevGraph& g, int k, long long o, int s0, int s1) {
     int pcd = 0;
     SCANP_RANGE(Grp, o, s0, s1)
-        int2 h[4];
+        uint32_t key[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) h[q] = w[q] >= 0 ? g.hc[w[q]] : make_int2(-1, 0);
+        for (int q = 0; q < 4; q++) key[q] = w[q] >= 0 ? g.kc[w[q]] : KEY_DEAD;
 #pragma unroll
-        for (int q = 0; q < 4; q++) pcd += (h[q].x > k) || (h[q].x == k && h[q].y > k);
+        for (int q = 0; q < 4; q++) pcd += key_core(key[q]) > k || (key_core(key[q]) == k && (key[q] & 1u));
     SCANP_END
     return pcd;
 }
@@ -615,6 +623,7 @@ __device__ __forceinline__ void evict_delete_vertex(const DevGraph& g, Ctl* C, c
     if constexpr (Grp::G > 32) __syncthreads();   // every warp has read k before it changes
     if (Grp::rank0()) {
         g.hc[v].x = k - 1;
+        g.kc[v] = key_of(k - 1, 0);   // bit set by the SD fix-up
         ls.ev++;
         ls.evl += len;
     }
@@ -639,14 +648,21 @@ __device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t 
             if (w[q] < 0) continue;
             sd += cw[q] >= kn;
             if (cw[q] == adj_core && g.chg[w[q]] != e) {
-                if (op == 0) atomicAdd(&g.hc[w[q]].y, 1);
-                else atomicSub(&g.hc[w[q]].y, 1);
+                // the key bit of w (SD > its core adj_core) moves with its SD:
+                // all of this phase's changes to w go the same way, so the
+                // update that crosses the core sets (insert) or clears it
+                if (op == 0) {
+                    if (atomicAdd(&g.hc[w[q]].y, 1) + 1 > adj_core) atomicOr(&g.kc[w[q]], 1u);
+                } else {
+                    if (atomicSub(&g.hc[w[q]].y, 1) - 1 <= adj_core) atomicAnd(&g.kc[w[q]], ~1u);
+                }
             }
         }
     SCAN4_END
     sd = Grp::sum(sd);
     if (Grp::rank0()) {
         g.hc[v].y = sd;
+        g.kc[v] = key_of(kn, sd);
         ls.ch++;
         ls.chl += len;
     }
