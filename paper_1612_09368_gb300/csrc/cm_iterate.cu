@@ -406,7 +406,18 @@ __device__ __forceinline__ void seed_tasks(Ctl* C, const MaintainParams& P, cons
 
 // An edge's core number k = min(core(lo), core(hi)) and its constrained
 // endpoints: those whose core is k (Definition 6), except pinned vertices.
-__device__ __forceinline__ void edge_level(const DevGraph& g, const REdge& E, int& k, bool& clo, bool& chi) {
+// An insertion never has pinned vertices (they exist only while a vertex
+// deletion removes their edges), so it reads the cores from the 4-byte keys.
+__device__ __forceinline__ void edge_level(const DevGraph& g, const REdge& E, bool ins, int& k, bool& clo,
+                                           bool& chi) {
+    if (ins) {
+        const int a = key_core(g.kc[E.lo]);
+        const int b = key_core(g.kc[E.hi]);
+        k = min(a, b);
+        clo = a == k;
+        chi = b == k;
+        return;
+    }
     const int2 a = g.hc[E.lo];
     const int2 b = g.hc[E.hi];
     k = min(a.x, b.x);
@@ -423,13 +434,14 @@ __device__ __forceinline__ unsigned long long edge_prio(const REdge& E, bool by_
 
 // Selection, claim phase of round r.  An edge already selected or blocked
 // that did not claim in round r-1 has nothing to do and gathers nothing.
-__device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e, bool by_key) {
+__device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e, bool by_key,
+                                           bool ins) {
     REdge E = R[i];
     const uint32_t f = E.flags;
     const bool claimed_last = r > 0 && (f >> 2) == (uint32_t)r;
     if ((f & (F_SEL | F_BLK)) && !claimed_last) return;
     int k; bool clo, chi;
-    edge_level(g, E, k, clo, chi);
+    edge_level(g, E, ins, k, clo, chi);
     if (claimed_last) {   // claimed in round r-1: clear that buffer
         unsigned long long* cb = ((r - 1) & 1) ? g.claim1 : g.claim0;
         if (clo) cb[E.lo] = CLAIM_FREE;
@@ -449,11 +461,11 @@ __device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long lon
 
 // Selection, check phase of round r.  Returns 1 if the edge claimed and lost.
 __device__ __forceinline__ int check_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e,
-                                          long long& nsel, bool by_key) {
+                                          long long& nsel, bool by_key, bool ins) {
     REdge E = R[i];
     if ((E.flags >> 2) != (uint32_t)(r + 1)) return 0;
     int k; bool clo, chi;
-    edge_level(g, E, k, clo, chi);
+    edge_level(g, E, ins, k, clo, chi);
     const unsigned long long prio = edge_prio(E, by_key);
     const unsigned long long* cb = (r & 1) ? g.claim1 : g.claim0;
     bool win = (!clo || cb[E.lo] == prio) && (!chi || cb[E.hi] == prio);
@@ -570,13 +582,13 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             if (MODE == 0 && r == 0) reset_tasks();   // nobody pushes tasks before APPLY
             for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
                 long long i = base + lane;
-                if (i < (long long)nrem) claim_edge(g, Rc, i, r, e, P.sel_key != 0);
+                if (i < (long long)nrem) claim_edge(g, Rc, i, r, e, P.sel_key != 0, P.op == 0);
             }
             if (!(ok = sync(PH_CLAIM))) break;
             int lost = 0;
             for (long long base = gwarp * 32; base < (long long)nrem; base += nwarps * 32) {
                 long long i = base + lane;
-                if (i < (long long)nrem) lost += check_edge(g, Rc, i, r, e, ls.sel, P.sel_key != 0);
+                if (i < (long long)nrem) lost += check_edge(g, Rc, i, r, e, ls.sel, P.sel_key != 0, P.op == 0);
             }
             lost = warp_sum(lost);
             if (lane == 0 && lost) atomicAdd(&C->pc[0], (unsigned long long)lost);
@@ -600,7 +612,7 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
                 E = Rc[i];
                 int k = 0; bool clo = false, chi = false;
                 // only a selected edge or one that claimed in the final round needs its level
-                if ((E.flags & F_SEL) || (E.flags >> 2) == (uint32_t)r) edge_level(g, E, k, clo, chi);
+                if ((E.flags & F_SEL) || (E.flags >> 2) == (uint32_t)r) edge_level(g, E, P.op == 0, k, clo, chi);
                 if ((E.flags >> 2) == (uint32_t)r) {     // claimed in the final round
                     unsigned long long* cb = ((r - 1) & 1) ? g.claim1 : g.claim0;
                     if (clo) cb[E.lo] = CLAIM_FREE;

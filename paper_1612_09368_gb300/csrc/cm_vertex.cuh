@@ -297,28 +297,26 @@ __device__ __forceinline__ void push_vertex4(Ctl* C, const MaintainParams& P, co
     if (ASYNC) __syncwarp();
 }
 
-// The words of a scan step's four neighbours as {core, SD, z, w}: core and SD
-// for every slot, then, in a second round of loads, the per-iteration word
-// only for the slots that can be candidates at level k (insert: core k and
-// SD > k; delete: core k and SD >= k); the others get z = w = 0, which no
-// body reads for a non-candidate.
+// The words of a scan step's four neighbours as {core, SD, z, w}.  First
+// the 4-byte key of every slot (core and whether SD > core), then, in a
+// second round of loads, only for the slots that can be candidates at level
+// k: the per-iteration word (insert: core k and SD > k) or the exact SD and
+// the per-iteration word (delete, whose threshold is SD - k + 1: core k).
+// The others get SD = core + the key bit and z = w = 0, which no body reads
+// for a non-candidate.
 __device__ __forceinline__ void gather4(const DevGraph& g, const int (&w)[4], int k, bool del, int4 (&h)[4]) {
+    uint32_t key[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) key[q] = w[q] >= 0 ? g.kc[w[q]] : KEY_DEAD;
     int2 c[4];
-    if (del) {   // deletion needs the exact SD (its threshold is SD - k + 1)
-#pragma unroll
-        for (int q = 0; q < 4; q++) c[q] = w[q] >= 0 ? g.hc[w[q]] : make_int2(-1, 0);
-    } else {     // insertion needs core and whether SD > core: the 4-byte key, SD as core + that bit
-        uint32_t key[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) key[q] = w[q] >= 0 ? g.kc[w[q]] : KEY_DEAD;
-#pragma unroll
-        for (int q = 0; q < 4; q++) c[q] = make_int2(key_core(key[q]), key_core(key[q]) + (int)(key[q] & 1u));
-    }
     unsigned long long s[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        const bool need = c[q].x == k && (del ? c[q].y >= k : c[q].y > k);
+        const int core = key_core(key[q]);
+        c[q] = make_int2(core, core + (int)(key[q] & 1u));
+        const bool need = core == k && (del || (key[q] & 1u));
         s[q] = need ? g.hw[w[q]] : 0ull;
+        if (del && need) c[q].y = g.hc[w[q]].y;
     }
 #pragma unroll
     for (int q = 0; q < 4; q++) h[q] = make_int4(c[q].x, c[q].y, (int)(uint32_t)s[q], (int)(uint32_t)(s[q] >> 32));
@@ -485,10 +483,10 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
                                                 long long o, int s0, int s1, uint32_t e) {
     SCANP_RANGE(Grp, o, s0, s1)
         int4 h[4];
+        gather4(g, w, k, true, h);
         uint32_t c[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) c[q] = w[q] >= 0 ? g.chg[w[q]] : 0u;
-        gather4(g, w, k, true, h);
+        for (int q = 0; q < 4; q++) c[q] = h[q].x == k ? g.chg[w[q]] : 0u;   // only core-k slots can be candidates
         bool cand[4], p[4];
         unsigned long long sw[4];
         uint32_t of[4];
@@ -637,12 +635,10 @@ __device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t 
     const int len = g.end[v];
     const int adj_core = op == 0 ? kn : kn + 1;   // neighbours whose SD counts v differently now
     int sd = 0;
-    SCAN4_BEGIN(Grp, len)
-        int w[4];
-        load4(g, o, len, t0_, w);
-        int cw[4];
+    SCANP_RANGE(Grp, o, 0, len)
+        int cw[4];   // cores from the keys (a core change rewrites the key with it)
 #pragma unroll
-        for (int q = 0; q < 4; q++) cw[q] = w[q] >= 0 ? g.hc[w[q]].x : -1;
+        for (int q = 0; q < 4; q++) cw[q] = w[q] >= 0 ? key_core(g.kc[w[q]]) : -1;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (w[q] < 0) continue;
@@ -658,7 +654,7 @@ __device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t 
                 }
             }
         }
-    SCAN4_END
+    SCANP_END
     sd = Grp::sum(sd);
     if (Grp::rank0()) {
         g.hc[v].y = sd;
