@@ -245,6 +245,14 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
+// A load with acquire semantics at device scope (later loads of this
+// thread see at least what the writer released before the loaded value).
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ unsigned long long vload64(const unsigned long long* p) {
     return *(const volatile unsigned long long*)p;
 }

@@ -329,7 +329,7 @@ __device__ __forceinline__ bool async_search(const DevGraph& g, Ctl* C, const Ma
                 }
                 if (poller) {
                     // quiescent: every task pushed has finished (done read first)
-                    const unsigned long long d = vload64(&C->task_done);
+                    const unsigned long long d = ld_acquire64(&C->task_done);   // read before the tail
                     if (d == vload64(&C->task_tail) || vload32(&C->error)) {
                         s_quiet = e;
                         quit = 1;
