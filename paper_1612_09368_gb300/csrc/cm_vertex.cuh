@@ -645,12 +645,12 @@ __device__ __forceinline__ void fixup_vertex(const DevGraph& g, int v, uint32_t 
             sd += cw[q] >= kn;
             if (cw[q] == adj_core && g.chg[w[q]] != e) {
                 // the key bit of w (SD > its core adj_core) moves with its SD:
-                // all of this phase's changes to w go the same way, so the
-                // update that crosses the core sets (insert) or clears it
+                // all of this phase's changes to w go the same way, so only
+                // the update that crosses the core sets (insert) or clears it
                 if (op == 0) {
-                    if (atomicAdd(&g.hc[w[q]].y, 1) + 1 > adj_core) atomicOr(&g.kc[w[q]], 1u);
+                    if (atomicAdd(&g.hc[w[q]].y, 1) == adj_core) atomicOr(&g.kc[w[q]], 1u);
                 } else {
-                    if (atomicSub(&g.hc[w[q]].y, 1) - 1 <= adj_core) atomicAnd(&g.kc[w[q]], ~1u);
+                    if (atomicSub(&g.hc[w[q]].y, 1) == adj_core + 1) atomicAnd(&g.kc[w[q]], ~1u);
                 }
             }
         }
