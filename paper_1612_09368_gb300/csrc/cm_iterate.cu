@@ -461,7 +461,7 @@ __device__ __forceinline__ void claim_edge(const DevGraph& g, REdge* R, long lon
 
 // Selection, check phase of round r.  Returns 1 if the edge claimed and lost.
 __device__ __forceinline__ int check_edge(const DevGraph& g, REdge* R, long long i, int r, uint32_t e,
-                                          long long& nsel, bool by_key, bool ins) {
+                                          uint32_t& nsel, bool by_key, bool ins) {
     REdge E = R[i];
     if ((E.flags >> 2) != (uint32_t)(r + 1)) return 0;
     int k; bool clo, chi;
@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
         }
     };
     LocalStats ls;
-    long long iters = 0, rounds = 0, waves = 0, remsum = 0;
+    int iters = 0, rounds = 0, waves = 0;   // per launch (a call is capped far below 2^31 iterations)
+    long long remsum = 0;
     // resume inside the search waves of an iteration the single-block mode began
     bool mid = *(volatile int*)&C->rs.mid != 0;
     bool escalate = false;

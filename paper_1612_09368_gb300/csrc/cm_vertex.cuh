@@ -25,8 +25,12 @@ namespace cm {
 
 constexpr uint32_t kVisited = 1u, kProcessed = 2u;
 
+// Per-warp counters of one launch, added to the control block's 64-bit
+// statistics when the launch ends.  32 bits each (registers are what the
+// grid kernel is short of): a warp's share of one launch stays far below
+// 2^32 vertices or list slots.
 struct LocalStats {
-    long long vis = 0, visl = 0, ev = 0, evl = 0, ch = 0, chl = 0, sel = 0;
+    uint32_t vis = 0, visl = 0, ev = 0, evl = 0, ch = 0, chl = 0, sel = 0;
 };
 
 // ---------------------------------------------------------------- per-iteration word
