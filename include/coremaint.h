@@ -116,6 +116,14 @@ typedef struct cm_options {
  * every warp's wait on the task queue runs out after spin_limit_ns and the
  * call returns CM_ERR_LIMIT (no fault, no hang). */
 #define CM_DEBUG_TASK_WAIT_NEVER_ENDS 4
+/* Debug mode, in effect while set (not cleared by a call): every update
+ * call of a single graph (edges and vertices, insert and delete) ends each
+ * maintenance launch after one superior-edge-set iteration and its SD
+ * fix-up, and runs cm_check on the store before the next; the first
+ * inconsistency fails the call with CM_ERR_LIMIT (handle poisoned).  The
+ * selected sets, iterations and cores are those of the normal mode.  Slow:
+ * for tests. */
+#define CM_DEBUG_CHECK_ITERATIONS 8
 
 /* Counters of the most recent update call (or of cm_recompute_cores). */
 typedef struct cm_stats {
@@ -217,6 +225,30 @@ int cm_get_cores(const cm_graph* g, int32_t* out, int32_t* n_total);
  * update call leaves it consistent with the cores it returns.  Same errors
  * as cm_get_cores. */
 int cm_get_superior_degrees(const cm_graph* g, int32_t* out, int32_t* n_total);
+
+/* Result of cm_check. */
+typedef struct cm_check_report {
+    int64_t vertices_checked;   /* every vertex id, live or dead */
+    int64_t sd_mismatches;      /* live vertices whose stored SD differs from a recount of Definition 7
+                                   (neighbours whose core is >= its own) */
+    int64_t key_mismatches;     /* vertices whose 4-byte scan key is not core << 1 | (SD > core), or not
+                                   the dead key for a deleted vertex */
+    int64_t degree_mismatches;  /* live vertices whose degree differs from the non-hole slots of their list */
+    int64_t bad_neighbour_ids;  /* list slots naming no live vertex */
+    int64_t kcore_violations;   /* live vertices with fewer than core(v) neighbours of core >= core(v)
+                                   (a k-core needs at least k of them, Definition 1) */
+    int64_t first_bad_vertex;   /* smallest vertex that failed a check, -1 if none */
+    int64_t reserved;
+} cm_check_report;
+
+/* Checks the device store against its own definitions, every vertex from
+ * scratch (a debug check; one pass over all lists, O(n + m)).  Vertices
+ * pinned by a vertex deletion in progress are not compared on SD, key or
+ * the k-core condition.  *out is filled and CM_OK returned whether or not
+ * mismatches were found; CM_ERR_STATE if the handle is poisoned or its cores
+ * are stale, CM_ERR_OOM if the 64-byte counter buffer cannot be allocated,
+ * CM_ERR_INVALID for NULL arguments.  Synchronises the handle's stream. */
+int cm_check(cm_graph* g, cm_check_report* out);
 
 /* Copies the current edge list (canonical pairs lo < hi, any order) into
  * host or device memory of capacity cap pairs; *m receives the edge count.

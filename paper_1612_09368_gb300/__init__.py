@@ -24,7 +24,8 @@ from . import build as _build
 __all__ = [
     "CM_OK", "CM_ERR_INVALID", "CM_ERR_OOM", "CM_ERR_CAPACITY", "CM_ERR_LIMIT", "CM_ERR_CUDA", "CM_ERR_STATE",
     "CM_OP_INSERT", "CM_OP_DELETE", "CM_DEBUG_BARRIER_NEVER_RELEASES", "CM_DEBUG_ITER_CAP",
-    "CM_DEBUG_TASK_WAIT_NEVER_ENDS", "CoreMaintError", "cm_options", "cm_stats",
+    "CM_DEBUG_TASK_WAIT_NEVER_ENDS", "CM_DEBUG_CHECK_ITERATIONS", "CoreMaintError", "cm_options", "cm_stats",
+    "cm_check_report", "cm_check",
     "lib", "library_path", "cm_default_options", "cm_create", "cm_create_multi", "cm_destroy", "cm_insert_edges",
     "cm_delete_edges", "cm_insert_vertices", "cm_insert_vertex", "cm_delete_vertices", "cm_delete_vertex",
     "cm_get_cores", "cm_get_superior_degrees", "cm_get_edges", "cm_num_vertices", "cm_num_edges", "cm_apply_edges", "cm_recompute_cores",
@@ -43,6 +44,7 @@ CM_OP_DELETE = 1
 CM_DEBUG_BARRIER_NEVER_RELEASES = 1
 CM_DEBUG_ITER_CAP = 2
 CM_DEBUG_TASK_WAIT_NEVER_ENDS = 4
+CM_DEBUG_CHECK_ITERATIONS = 8
 CM_SELECT_HASH = 0
 CM_SELECT_KEY = 1
 
@@ -76,6 +78,12 @@ class cm_stats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "phase_ns")}
         d["phase_ns"] = dict(zip(self.PHASES, list(self.phase_ns)))
         return d
+
+
+class cm_check_report(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "vertices_checked", "sd_mismatches", "key_mismatches", "degree_mismatches", "bad_neighbour_ids",
+        "kcore_violations", "first_bad_vertex", "reserved")]
 
 
 class cm_step_config(ctypes.Structure):
@@ -145,6 +153,7 @@ def lib():
             "cm_get_cores": (ctypes.c_int, [vp, vp, p32]),
             "cm_get_edges": (ctypes.c_int, [vp, vp, i64, p64]),
             "cm_get_superior_degrees": (ctypes.c_int, [vp, vp, p32]),
+            "cm_check": (ctypes.c_int, [vp, ctypes.POINTER(cm_check_report)]),
             "cm_num_vertices": (i32, [vp]),
             "cm_num_edges": (i64, [vp]),
             "cm_apply_edges": (ctypes.c_int, [vp, i32, vp, i64, p64]),
@@ -365,6 +374,15 @@ def cm_get_superior_degrees(h, out=None):
     return out
 
 
+def cm_check(h) -> dict:
+    """Consistency of the device store with its definitions (SD recount,
+    scan keys, degrees, neighbour ids, the k-core condition), as a dict of
+    cm_check_report's fields."""
+    r = cm_check_report()
+    _check(h, lib().cm_check(h, ctypes.byref(r)), "cm_check")
+    return {name: getattr(r, name) for name, _ in r._fields_ if name != "reserved"}
+
+
 def cm_get_edges(h) -> np.ndarray:
     m = cm_num_edges(h)
     out = np.empty((max(m, 0), 2), dtype=np.int32)
@@ -555,6 +573,9 @@ class CoreGraph:
 
     def superior_degrees(self, out=None):
         return cm_get_superior_degrees(self._h, out)
+
+    def check(self) -> dict:
+        return cm_check(self._h)
 
     def edges(self) -> np.ndarray:
         return cm_get_edges(self._h)

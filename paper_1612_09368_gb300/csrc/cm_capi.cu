@@ -59,6 +59,7 @@ struct cm_graph {
     int32_t* dbases = nullptr;
     long long* dprefix = nullptr;
     unsigned long long* dpergraph = nullptr;
+    unsigned long long* dchk = nullptr;   // counters of the consistency check (allocated on first use)
     // timing and counters
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cm_stats last{};
@@ -395,6 +396,7 @@ static void free_all(cm_graph* h) {
     if (h->dbases) cudaFree(h->dbases);
     if (h->dprefix) cudaFree(h->dprefix);
     if (h->dpergraph) cudaFree(h->dpergraph);
+    if (h->dchk) cudaFree(h->dchk);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);
     for (auto& e : h->ev)
@@ -403,6 +405,8 @@ static void free_all(cm_graph* h) {
 }
 
 static int peel_all(cm_graph* h);
+static int run_check(cm_graph* h, cm_check_report* r);
+static bool check_clean(const cm_check_report& r);
 
 // Builds the store from a device edge list (global ids).
 static int build_store(cm_graph* h, const int32_t* dE, long long m, const int32_t* dcores) {
@@ -799,6 +803,9 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
             p.small_edges = -1;
             h->opt.debug_flags &= ~CM_DEBUG_TASK_WAIT_NEVER_ENDS;
         }
+        // debug mode: one iteration per launch pair, the store checked after each
+        const bool check_each = (h->opt.debug_flags & CM_DEBUG_CHECK_ITERATIONS) != 0;
+        p.yield_each = check_each ? 1 : 0;
         // where the call starts: all kept edges remain, in R0
         Resume rs{};
         rs.nrem = (unsigned long long)nrem0;   // replaced on the device by ingest's count (device_count)
@@ -815,13 +822,26 @@ static int update_device(cm_graph* h, int op, const int32_t* dE, long long k, in
         // the other returns at once; a handover inside the pair needs no host.
         bool want_grid = rs.want == 0;
         for (int pass = 0;; pass++) {
-            if (pass >= 256) {
+            if (pass >= (check_each ? (1 << 24) : 256)) {
                 h->poisoned = true;
-                return set_err(h, CM_ERR_LIMIT, "maintenance did not finish within 256 launch pairs");
+                return set_err(h, CM_ERR_LIMIT, "maintenance did not finish within %d launch pairs", pass);
             }
             if (want_grid) LAUNCH(h, launch_maintain(p, blocks, threads, h->stream));
             LAUNCH(h, launch_maintain_block(p, 1024, h->stream));
             if ((rc = rd_ctl(h))) return rc;
+            if (check_each && !c.error) {
+                cm_check_report r{};
+                if ((rc = run_check(h, &r))) return rc;
+                if (!check_clean(r)) {
+                    h->poisoned = true;
+                    return set_err(h, CM_ERR_LIMIT,
+                                   "consistency check failed after iteration %d: %lld SD, %lld key, %lld degree, "
+                                   "%lld neighbour-id, %lld k-core mismatches (first vertex %lld)",
+                                   pass + 1, (long long)r.sd_mismatches, (long long)r.key_mismatches,
+                                   (long long)r.degree_mismatches, (long long)r.bad_neighbour_ids,
+                                   (long long)r.kcore_violations, (long long)r.first_bad_vertex);
+                }
+            }
             if (c.error || c.rs.done) break;
             want_grid = c.rs.want == 0;
         }
@@ -1078,6 +1098,44 @@ extern "C" int cm_get_superior_degrees(const cm_graph* hc, int32_t* out, int32_t
     CK(h, cudaMemcpyAsync(out, h->CQ, (size_t)h->n * 4, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return CM_OK;
+}
+
+// ------------------------------------------------------------------ consistency check
+static int run_check(cm_graph* h, cm_check_report* r) {
+    if (!h->dchk) {
+        if (cudaMalloc(&h->dchk, 8 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            h->dchk = nullptr;
+            return set_err(h, CM_ERR_OOM, "out of device memory for the check counters");
+        }
+    }
+    DevGraph g = h->g;
+    g.n = h->n;
+    LAUNCH(h, check_store(g, h->dchk, h->stream));
+    unsigned long long v[7];
+    CK(h, cudaMemcpyAsync(v, h->dchk, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    r->sd_mismatches = (int64_t)v[0];
+    r->key_mismatches = (int64_t)v[1];
+    r->degree_mismatches = (int64_t)v[2];
+    r->bad_neighbour_ids = (int64_t)v[3];
+    r->kcore_violations = (int64_t)v[4];
+    r->vertices_checked = (int64_t)v[5];
+    r->first_bad_vertex = v[6] == ~0ull ? -1 : (int64_t)v[6];
+    return CM_OK;
+}
+
+static bool check_clean(const cm_check_report& r) {
+    return r.sd_mismatches == 0 && r.key_mismatches == 0 && r.degree_mismatches == 0 && r.bad_neighbour_ids == 0 &&
+           r.kcore_violations == 0;
+}
+
+extern "C" int cm_check(cm_graph* h, cm_check_report* out) {
+    if (!h || !out) return CM_ERR_INVALID;
+    if (h->poisoned) return set_err(h, CM_ERR_STATE, "handle poisoned: %s", h->err.c_str());
+    if (h->cores_stale) return set_err(h, CM_ERR_STATE, "cores are stale: call cm_recompute_cores");
+    memset(out, 0, sizeof(*out));
+    return run_check(h, out);
 }
 
 extern "C" int cm_get_edges(const cm_graph* hc, int32_t* out, int64_t cap, int64_t* m) {

@@ -801,6 +801,10 @@ __global__ void __launch_bounds__(MODE == 0 ? kGridThreads : kBlockThreads, MODE
             finished = 1;
             break;
         }
+        if (P.yield_each) {   // debug: end the launch here (the fix-up below still runs); resume in this mode
+            next_want = MODE;
+            break;
+        }
         if (MODE == 0 && nrem <= (unsigned long long)P.small_edges && work <= (unsigned long long)P.small_work) {
             next_want = 1;
             break;

@@ -45,7 +45,7 @@ struct MaintainParams {
     int32_t use_cond;         // inside a captured step: the single-block kernel drives the loop node
     int32_t phantom_task;     // test hook: every grid search counts one task that is never queued
     int32_t expand_early;     // frontier expansion in the CSD pass: >= 0 yes (default), -1 after it (paper's order)
-    int32_t pad_;
+    int32_t yield_each;       // debug: end the launch after every iteration (its SD fix-up done)
     unsigned long long cond;  // that node's conditional handle
 };
 
@@ -113,6 +113,7 @@ cudaError_t mark_dead(const int32_t* ids, int32_t count, DevGraph g, cudaStream_
 cudaError_t pin_vertices(const int32_t* ids, int32_t count, DevGraph g, cudaStream_t s);
 cudaError_t export_cores(DevGraph g, int32_t* out, cudaStream_t s);
 cudaError_t export_sd(DevGraph g, int32_t* out, cudaStream_t s);
+cudaError_t check_store(DevGraph g, unsigned long long* out, cudaStream_t s);
 cudaError_t export_edges(DevGraph g, int32_t* out, Ctl* c, cudaStream_t s);
 cudaError_t localize_multi(int32_t* E, long long k, const unsigned long long* kp, const long long* prefix,
                            const int32_t* bases, int32_t ng, cudaStream_t s);

@@ -709,6 +709,92 @@ __global__ void export_edges_kernel(DevGraph g, int2* out, Ctl* c) {
     }
 }
 
+// Consistency of the store with its own definitions (a debug check, run on
+// request).  Per live vertex v, from its list: SD (Definition 7) recounted
+// from the neighbours' cores against hc[v].y; the scan key against core and
+// the stored SD; the live degree against the list's non-hole slots; every
+// slot a hole or a live vertex id; and the k-core condition (at least
+// core(v) neighbours of core >= core(v)).  A pinned vertex (vertex deletion
+// in progress) keeps its pinned SD and is not compared on SD, key or the
+// k-core condition.  A dead vertex must carry the dead key.  Warp per
+// vertex; out[0..4] count the mismatches of the five checks, out[5] the
+// vertices checked, out[6] the smallest vertex that failed a check.
+__global__ void check_store_kernel(DevGraph g, unsigned long long* out) {
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int lane = lane_id();
+    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < g.n; v += nw) {
+        const int2 h = g.hc[v];
+        const uint32_t key = g.kc[v];
+        if (h.x < 0) {
+            if (lane == 0) {
+                atomicAdd(&out[5], 1ull);
+                if (key != KEY_DEAD) {
+                    atomicAdd(&out[1], 1ull);
+                    atomicMin(&out[6], (unsigned long long)v);
+                }
+            }
+            continue;
+        }
+        const long long o = g.off[v];
+        const int len = g.end[v];
+        int sd = 0, live = 0, bad = 0;
+        for (int t = lane; t < len; t += 32) {
+            const int w = g.adj[o + t];
+            if (w == HOLE) continue;
+            if (w < 0 || w >= g.n) {
+                bad++;
+                continue;
+            }
+            const int cw = g.hc[w].x;
+            if (cw < 0) {
+                bad++;
+                continue;
+            }
+            live++;
+            sd += cw >= h.x;
+        }
+        sd = warp_sum(sd);
+        live = warp_sum(live);
+        bad = warp_sum(bad);
+        if (lane == 0) {
+            const bool pinned = h.y == PIN_SD;
+            bool fail = false;
+            if (!pinned && sd != h.y) {
+                atomicAdd(&out[0], 1ull);
+                fail = true;
+            }
+            if (!pinned && key != key_of(h.x, h.y)) {
+                atomicAdd(&out[1], 1ull);
+                fail = true;
+            }
+            if (live != g.deg[v]) {
+                atomicAdd(&out[2], 1ull);
+                fail = true;
+            }
+            if (bad) {
+                atomicAdd(&out[3], (unsigned long long)bad);
+                fail = true;
+            }
+            if (!pinned && sd < h.x) {
+                atomicAdd(&out[4], 1ull);
+                fail = true;
+            }
+            atomicAdd(&out[5], 1ull);
+            if (fail) atomicMin(&out[6], (unsigned long long)v);
+        }
+    }
+}
+
+cudaError_t check_store(DevGraph g, unsigned long long* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 6 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(out + 6, 0xFF, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (g.n <= 0) return cudaSuccess;
+    check_store_kernel<<<grid_for((long long)g.n * 32, 256, 65536), 256, 0, s>>>(g, out);
+    return cudaGetLastError();
+}
+
 cudaError_t export_cores(DevGraph g, int32_t* out, cudaStream_t s) {
     if (g.n <= 0) return cudaSuccess;
     export_cores_kernel<<<grid_for(g.n, 256, 1ll << 31), 256, 0, s>>>(g, out);

@@ -36,6 +36,8 @@ def test_binding_struct_layouts_match_header():
     assert ctypes.sizeof(cm.cm_step_config) == 8 * 4
     # cm_stats: 14 int64, 2 double, peel_levels, barriers, grid_iterations, phase_ns[7], reserved[4]
     assert ctypes.sizeof(cm.cm_stats) == 14 * 8 + 2 * 8 + (3 + 7 + 4) * 8
+    # cm_check_report: 8 int64 (vertices checked, five mismatch counts, first bad vertex, reserved)
+    assert ctypes.sizeof(cm.cm_check_report) == 8 * 8
 
 
 def test_default_options_without_gpu(so):
