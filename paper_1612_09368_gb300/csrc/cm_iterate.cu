@@ -91,8 +91,11 @@ struct Barrier {
 };
 
 // ---------------------------------------------------------------- vertex loop (waves)
-// Runs body(v, Group) for every vertex of ring[lo, hi): one warp per vertex
-// with dynamic fetching (counter *ctr, zeroed at every barrier).  A vertex
+// Runs body(v, Group) for every vertex of ring[lo, hi): one warp per vertex.
+// Each warp's first vertex is dealt by its warp index; the rest are fetched
+// dynamically (counter *ctr, zeroed at every barrier), so a phase with no
+// more vertices than warps touches no shared counter, and a larger one does
+// not start with every warp of the grid at the same counter.  A vertex
 // with at least P.block_len slots (kBlockLenSingle in single-block mode) is
 // deferred by the warp that fetched it and then processed by that warp's
 // whole block, so a long list does not hold a wave on one warp.  Every
@@ -107,11 +110,11 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, const Maintai
     __shared__ int s_nbig;
     if (threadIdx.x == 0) s_nbig = 0;
     __syncthreads();
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long cnt = hi - lo;
+    unsigned long long j = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     for (;;) {
-        unsigned long long j = 0;
-        if (lane == 0) j = atomicAdd(ctr, 1ull);
-        j = __shfl_sync(0xffffffffu, j, 0);
-        if (j >= hi - lo) break;
+        if (j >= cnt) break;
         const int v = ring[(lo + j) & qm];
         int defer = 0;
         if (lane == 0 && g.end[v] >= (MODE == 0 ? P.block_len : kBlockLenSingle)) {
@@ -121,8 +124,10 @@ __device__ __forceinline__ void for_each_vertex(const DevGraph& g, const Maintai
                 defer = 1;
             }
         }
-        if (__shfl_sync(0xffffffffu, defer, 0)) continue;
-        body(v, WarpGroup{});
+        if (!__shfl_sync(0xffffffffu, defer, 0)) body(v, WarpGroup{});
+        if (cnt <= nw) break;   // every vertex was dealt by index
+        if (lane == 0) j = nw + atomicAdd(ctr, 1ull);
+        j = __shfl_sync(0xffffffffu, j, 0);
     }
     __syncthreads();
     const int nb = min(s_nbig, kMaxBig);
