@@ -3,10 +3,9 @@
 // Device layout of one graph (all arrays indexed by vertex id unless noted):
 //   hc[v]   int2  {core, SD}: core is the core number (-1 dead); SD is the
 //           superior degree (Section IV, Definition 7: neighbours with core
-//           >= core(v)).  Every scan step gathers these 8 bytes per
-//           neighbour; at 2^24 vertices the array is half the size of a
-//           16-byte word per vertex, so twice as much of it stays in L2 and a
-//           32-byte sector carries four vertices instead of two.
+//           >= core(v)).  Scans read it only where the exact SD matters
+//           (a core-k neighbour in a deletion scan, an edge level during a
+//           deletion); everything else reads the key kc below.
 //   hw[v]   u64   the per-iteration word: low 32 bits a stamp (iteration << 2
 //           | flags), high 32 bits a count (insert: visited / processed
 //           flags and support; delete: evicted-neighbour count).  Scans load

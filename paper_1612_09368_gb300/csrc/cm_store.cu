@@ -100,7 +100,7 @@ __global__ void set_cores_kernel(const int32_t* __restrict__ cores, DevGraph g) 
 // 16-byte aligned and their capacity is a multiple of 4) and the four
 // neighbour gathers issued before any is used.  The cores are read from a
 // compact copy (4 bytes per vertex, which stays in L2 at the sizes here)
-// instead of the 16-byte vertex words.
+// instead of the 8-byte {core, SD} words.
 __global__ void copy_cores_kernel(DevGraph g, int32_t* core) {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= g.n) return;
@@ -176,8 +176,8 @@ cudaError_t init_mcd(DevGraph g, int32_t v0, int32_t v1, int32_t* core_scratch, 
 // exactly when its degree reaches k (the decrement from k + 1 to k, or the
 // level's scan finding it at k).  So at the scan of level k every remaining
 // vertex has degree >= k and every vertex that left has degree < k: the
-// scan reads the working degree alone (never the 16-byte vertex word) to
-// tell the three cases apart.
+// scan reads the working degree alone (never the vertex's {core, SD} word)
+// to tell the three cases apart.
 //
 // A frontier vertex with at least kPeelBig slots is not scanned by the warp
 // that takes it: its list is cut into kPeelChunk-slot chunk tasks that every

@@ -330,7 +330,7 @@ __device__ __forceinline__ void gather4(const DevGraph& g, const int (&w)[4], in
 // slots at or past len).
 __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, int t0, int w[4]) {
     int4 a = make_int4(HOLE, HOLE, HOLE, HOLE);
-    if (t0 < len) a = __ldcs(reinterpret_cast<const int4*>(g.adj + o + t0));   // streamed: keep L2 for vertex words
+    if (t0 < len) a = __ldcs(reinterpret_cast<const int4*>(g.adj + o + t0));   // streamed: keep L2 for the keys
     w[0] = a.x;
     w[1] = t0 + 1 < len ? a.y : HOLE;
     w[2] = t0 + 2 < len ? a.z : HOLE;
@@ -347,7 +347,7 @@ __device__ __forceinline__ void load4(const DevGraph& g, long long o, int len, i
 // The same walk with the list read two steps ahead: each lane loads the
 // 16-byte words of two consecutive steps before the first step's gathers,
 // so a step's neighbour gathers do not wait behind its own list read.  List
-// reads are streamed (evict-first) so that L2 keeps the vertex words.
+// reads are streamed (evict-first) so that L2 keeps the per-vertex keys.
 // Inside, `int w[4]` holds the step's four neighbour ids (HOLE past s1)
 // and `last_` is set in the group's last step.
 #define SCANP_RANGE(Grp, o, s0, s1)                                                              \
@@ -515,8 +515,8 @@ __device__ __forceinline__ void evict_del_range(const DevGraph& g, Ctl* C, const
 }
 
 // ---------------------------------------------------------------- per-vertex phase bodies
-// A task's vertex: its 16-byte word, list offset and length, loaded
-// together (three independent loads) before anything uses them.
+// A task's vertex: {core, SD}, its per-iteration word, list offset and
+// length, loaded together (independent loads) before anything uses them.
 struct VInfo {
     int4 h;
     long long o;
