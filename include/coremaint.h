@@ -461,7 +461,8 @@ void cm_server_destroy(cm_server* s);
  * in both endpoints' rows).  cores (device, n int32) receives the result.
  * Runs on `stream` (cudaStream_t) and returns after completion.  It
  * allocates nothing: its scratch is one static device array sized for at
- * most 1,048,576 vertices (16 MiB plus a 4 KiB control block), held by every
+ * most 1,048,576 vertices (16 MiB, plus 2 MiB of chunk tasks for the lists
+ * of high-degree vertices and a 4 KiB control block), held by every
  * GPU that loads the library until the process exits.  All calls share that
  * array: calls whose work overlaps on the GPU (for example on two streams)
  * race on it and must not be issued.  The first call on a device looks up

@@ -25,7 +25,12 @@ namespace cm {
 
 constexpr int32_t kMaxVertices = 1 << 20;
 constexpr size_t kCtlBytes = 4096;
-constexpr size_t kScratchBytes = kCtlBytes + 4ull * sizeof(int32_t) * kMaxVertices;   // Ctl + 4 int32 per vertex
+constexpr int kBigDegree = 2048;                  // a vertex this large is scanned in chunk tasks
+constexpr int kChunkSlots = 512;                  // slots per chunk task
+constexpr unsigned long long kMaxChunks = 1 << 18;   // chunk tasks per sub-wave (more: the warp scans alone)
+constexpr unsigned long long kNoChunk = ~0ull;
+// Ctl, 4 int32 per vertex, then the chunk tasks of a sub-wave
+constexpr size_t kScratchBytes = kCtlBytes + 4ull * sizeof(int32_t) * kMaxVertices + kMaxChunks * 8;
 static_assert(sizeof(Ctl) <= kCtlBytes, "control block does not fit");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -46,13 +51,18 @@ struct PeelCsrParams {
 // as the store's full decomposition): at level k every remaining vertex with
 // degree <= k gets core k and leaves, taking one degree from each remaining
 // neighbour; neighbours that reach k leave at the same level; empty levels
-// are skipped to the smallest remaining degree.
+// are skipped to the smallest remaining degree.  A departing vertex of at
+// least kBigDegree neighbours is not scanned by the warp that takes it: its
+// list becomes kChunkSlots-slot chunk tasks that every warp takes after the
+// sub-wave's barrier, so one hub does not hold the whole grid at the next
+// barrier.
 __global__ void __launch_bounds__(512) peel_csr_kernel(PeelCsrParams P) {
     Ctl* C = reinterpret_cast<Ctl*>(P.scratch);
     int32_t* dcur = reinterpret_cast<int32_t*>(P.scratch + kCtlBytes);
     int32_t* L0 = dcur + kMaxVertices;
     int32_t* L1 = L0 + kMaxVertices;
     int32_t* F = L1 + kMaxVertices;
+    unsigned long long* chunks = reinterpret_cast<unsigned long long*>(F + kMaxVertices);
     const int lane = lane_id();
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -109,6 +119,22 @@ __global__ void __launch_bounds__(512) peel_csr_kernel(PeelCsrParams P) {
             k = 0x7FFFFFFF - (int)smx;
             continue;
         }
+        // one degree off every unpeeled neighbour in list slots [a, b); a
+        // neighbour brought to k leaves now and joins the frontier
+        auto decrement = [&](long long a, long long b) {
+            for (long long t0 = a; t0 < b; t0 += 32) {
+                long long tt = t0 + lane;
+                int w = tt < b ? P.adj[tt] : -1;
+                bool p = false;
+                if (w >= 0 && w < P.n && P.cores[w] == kNoallocUnpeeled) {
+                    if (atomicSub(&dcur[w], 1) == k + 1) {
+                        P.cores[w] = k;
+                        p = true;
+                    }
+                }
+                warp_push(&C->tail[0], F, ~0ull, p, w);
+            }
+        };
         unsigned long long lo = f0, hi = fhi;
         while (hi > lo) {
             const unsigned long long cnt = hi - lo;
@@ -119,20 +145,31 @@ __global__ void __launch_bounds__(512) peel_csr_kernel(PeelCsrParams P) {
                 if (j >= cnt) break;
                 const int v = F[lo + j];
                 const long long a = P.row_off[v], b = P.row_off[v + 1];
-                for (long long t0 = a; t0 < b; t0 += 32) {
-                    long long tt = t0 + lane;
-                    int w = tt < b ? P.adj[tt] : -1;
-                    bool p = false;
-                    if (w >= 0 && w < P.n && P.cores[w] == kNoallocUnpeeled) {
-                        if (atomicSub(&dcur[w], 1) == k + 1) {
-                            P.cores[w] = k;
-                            p = true;
-                        }
-                    }
-                    warp_push(&C->tail[0], F, ~0ull, p, w);
+                if (b - a >= kBigDegree) {   // chunk tasks (vertex, chunk), counted in pc[0]
+                    const unsigned long long nch = (unsigned long long)((b - a + kChunkSlots - 1) / kChunkSlots);
+                    unsigned long long tb = 0;
+                    if (lane == 0) tb = atomicAdd(&C->pc[0], nch);
+                    tb = __shfl_sync(0xffffffffu, tb, 0);
+                    const bool fits = tb + nch <= kMaxChunks;
+                    for (unsigned long long c = lane; c < nch && tb + c < kMaxChunks; c += 32)
+                        chunks[tb + c] = fits ? (((unsigned long long)(uint32_t)v << 32) | (uint32_t)c) : kNoChunk;
+                    if (fits) continue;
                 }
+                decrement(a, b);
             }
             if (!grid_sync(C, P.expect, P.limit_ns)) return;
+            const unsigned long long nch = min(vload64(&C->spc[0]), kMaxChunks);
+            if (nch > 0) {
+                for (unsigned long long c = (unsigned long long)gwarp; c < nch; c += (unsigned long long)nwarps) {
+                    const unsigned long long task = chunks[c];
+                    if (task == kNoChunk) continue;
+                    const int v = (int)(task >> 32);
+                    const long long a = P.row_off[v] + (long long)(task & 0xFFFFFFFFu) * kChunkSlots;
+                    const long long end = P.row_off[v + 1];
+                    decrement(a, a + kChunkSlots < end ? a + (long long)kChunkSlots : end);
+                }
+                if (!grid_sync(C, P.expect, P.limit_ns)) return;
+            }
             lo = hi;
             hi = vload64(&C->stail[0]);
         }
