@@ -89,10 +89,14 @@ __global__ void scatter_kernel(const int32_t* __restrict__ E, const uint32_t* __
     g.idx[b].shi = pv;
 }
 
+// Given cores (a checkpoint): core -1 marks a deleted vertex, which gets the
+// dead key; a live vertex's key bit is set by the SD pass that follows.
 __global__ void set_cores_kernel(const int32_t* __restrict__ cores, DevGraph g) {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= g.n) return;
-    g.hc[v].x = cores[v];
+    const int c = cores[v];
+    g.hc[v].x = c;
+    g.kc[v] = c < 0 ? KEY_DEAD : key_of(c, 0);
 }
 
 // SD(v), Definition 7: neighbours with core >= core(v).  Warp per vertex;

@@ -112,3 +112,7 @@ def test_debug_mode_vertex_operations(cm):
         alive[dead] = False
         assert (g.cores() == ref.cores()).all(), r
         _clean(g.check(), len(alive), f"round {r}")
+    # a checkpoint with deleted vertices (core -1) resumes into a consistent store
+    g2 = cm.CoreGraph(len(alive), _dev(g.edges()), _dev(g.cores()))
+    _clean(g2.check(), len(alive), "resumed")
+    assert (g2.cores() == ref.cores()).all()
