@@ -283,6 +283,60 @@ __device__ __forceinline__ void peel_range(const DevGraph& g, const PeelParams& 
     }
 }
 
+// The peel's grid barrier.  The contract of grid_sync (the last block to
+// arrive copies the live tails and phase counters into their snapshots and
+// zeroes the counters before it releases the others; false once an error
+// is recorded), with the ordering carried by the operations themselves: the
+// arrival is an acquire-release add, the release a release store that also
+// carries the error state, each waiter's poll an acquire load.  The peel
+// runs ~5 barrier-separated phases per level, so the barrier's critical
+// path (last arrival, snapshot, release, the waiters' next poll) is a large
+// part of its time.  The release word is (generation << 1) | error; the
+// launch zone is zeroed before every peel launch.
+__device__ __forceinline__ bool peel_sync(Ctl* c, unsigned int expect, unsigned long long limit_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;" : "=l"(t) : "l"(&c->arrive) : "memory");
+        const unsigned long long gen = t / expect;
+        int ok = 1;
+        if (t % expect == expect - 1) {
+            for (int i = 0; i < kTails; i++) {
+                c->stail[i] = vload64(&c->tail[i]);
+                c->spc[i] = vload64(&c->pc[i]);
+                c->pc[i] = 0;
+            }
+            ok = vload32(&c->error) == 0;
+            const unsigned long long rel = ((gen + 1) << 1) | (ok ? 0ull : 1ull);
+            asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&c->release), "l"(rel) : "memory");
+        } else {
+            const unsigned long long t0 = gtimer();
+            unsigned int spins = 0;
+            for (;;) {
+                const unsigned long long rel = ld_acquire64(&c->release);
+                if ((rel >> 1) >= gen + 1) {
+                    ok = (rel & 1ull) == 0;
+                    break;
+                }
+                if (vload32(&c->error)) {
+                    ok = 0;
+                    break;
+                }
+                if ((++spins & 63u) == 0 && gtimer() - t0 > limit_ns) {
+                    atomicCAS(&c->error, 0, E_BARRIER_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // Phases of the peel timed at its barriers (block 0's view, into Ctl::ph):
 // the level scans, the sub-waves and the chunk phases.
 enum { PP_SCAN = 0, PP_WAVE = 1, PP_CHUNK = 2 };
@@ -291,7 +345,7 @@ struct PeelClock {
     unsigned long long t;
     bool on;
     __device__ bool sync(const PeelParams& P, int phase) {
-        const bool ok = grid_sync(c, P.expect, P.limit_ns);
+        const bool ok = peel_sync(c, P.expect, P.limit_ns);
         if (on) {
             const unsigned long long now = gtimer();
             c->ph[phase] += now - t;
