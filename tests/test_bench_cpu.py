@@ -62,3 +62,24 @@ def test_sweep_o3_rates_restore_the_oracle_graph():
     assert all(d >= 1 for d, t in r.values()) and all(offsets[k] == r[k][0] for k in r)
     assert (og.cores() == c0).all() and og.m == m0
     assert (og.cores() == oracle.bz(n, e)).all()
+
+
+def test_reference_arm_prints_one_line_on_a_small_sweep():
+    """The reference arm (the oracle on host cores) on a small R-MAT sweep:
+    one JSON line carrying the sweep's metric, its own CPU baseline and an
+    e2e record, with no GPU needed."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--scale", "12", "--sizes", "100,1000",
+                        "--steps", "1", "--warmup", "1", "--ref-budget", "0.2"],
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))), capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["config"]["workload"] == "rmat12-sweep"
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
