@@ -367,7 +367,6 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
     const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
     int32_t* buf = S.buf[wib];
     int cnt = 0;
-    bool ok;
     PeelClock clk{C, gtimer(), blockIdx.x == 0 && threadIdx.x == 0};
     // live vertices start unpeeled with their live degree (compacted into
     // the remaining list a tile at a time, like the level scans below)
@@ -397,7 +396,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
         for (int j = threadIdx.x; j < S.nkeep; j += kPeelThreads) P.L0[S.kbase + j] = S.keep[j];
         __syncthreads();
     }
-    if (!(ok = clk.sync(P, PP_SCAN))) return;
+    if (!clk.sync(P, PP_SCAN)) return;
     unsigned long long nl = vload64(&C->spc[1]);
     int32_t* Lc = P.L0;
     int32_t* Ln = P.L1;
@@ -460,7 +459,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
             for (int j = threadIdx.x; j < S.npeel; j += kPeelThreads) P.F[S.pbase + j] = S.peel[j];
             __syncthreads();
         }
-        if (!(ok = clk.sync(P, PP_SCAN))) return;
+        if (!clk.sync(P, PP_SCAN)) return;
         unsigned long long fhi = vload64(&C->stail[0]);
         unsigned long long nln = vload64(&C->spc[1]);
         unsigned long long smx = vload64(&C->spc[3]);
@@ -502,7 +501,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
                 peel_range(g, P, C, o, 0, len, k, buf, cnt);
             }
             block_flush_peeled(C, P, S, cnt);
-            if (!(ok = clk.sync(P, PP_WAVE))) return;
+            if (!clk.sync(P, PP_WAVE)) return;
             const unsigned long long nchunks = min(vload64(&C->spc[3]), P.chunk_cap);
             if (nchunks > 0) {
                 for (unsigned long long c = (unsigned long long)gwarp; c < nchunks; c += (unsigned long long)nwarps) {
@@ -513,7 +512,7 @@ __global__ void __launch_bounds__(kPeelThreads) peel_kernel(PeelParams P) {
                     peel_range(g, P, C, g.off[v], s0, min(g.end[v], s0 + kPeelChunk), k, buf, cnt);
                 }
                 block_flush_peeled(C, P, S, cnt);
-                if (!(ok = clk.sync(P, PP_CHUNK))) return;
+                if (!clk.sync(P, PP_CHUNK)) return;
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) C->st[ST_WAVES]++;
             lo = hi;
